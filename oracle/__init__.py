@@ -65,6 +65,7 @@ def _load():
     lib.or_eri_primitive.restype = ctypes.c_double
     lib.or_eri_primitive.argtypes = [_ip, ctypes.c_double, _dp] * 4
     lib.or_schwarz.argtypes = [ctypes.c_void_p, _dp]
+    lib.or_one_electron_primitive.argtypes = [_ip, ctypes.c_double, _dp, _ip, ctypes.c_double, _dp, ctypes.c_double, _dp, _dp]
     lib.or_packed_size.restype = ctypes.c_int64
     lib.or_packed_size.argtypes = [ctypes.c_void_p]
     lib.or_eri_packed.argtypes = [ctypes.c_void_p, _dp]
@@ -104,6 +105,15 @@ def eri_primitive(pa, a, A, pb, b, B, pc, c, C, pd, d, D) -> float:
         arrays += [pwa, ca]
         cargs += [_i(pwa), float(ex), _d(ca)]
     return float(_load().or_eri_primitive(*cargs))
+
+
+def one_electron_primitive(pa, a, A, pb, b, B, Zc, C):
+    """Unnormalised primitive (S, T, V_C) for one pair and one point charge Zc at C."""
+    pa_, pb_ = np.ascontiguousarray(pa, dtype=np.int32), np.ascontiguousarray(pb, dtype=np.int32)
+    A_, B_, C_ = (np.ascontiguousarray(x, dtype=np.float64) for x in (A, B, C))
+    out = np.zeros(3)
+    _load().or_one_electron_primitive(_i(pa_), float(a), _d(A_), _i(pb_), float(b), _d(B_), float(Zc), _d(C_), _d(out))
+    return out
 
 
 class Molecule:

@@ -321,6 +321,39 @@ void or_one_electron(void* h, double* S, double* T, double* V)
     }
 }
 
+/*
+ * One unnormalised primitive pair: out[0] = overlap, out[1] = kinetic energy,
+ * out[2] = attraction to a point charge Zc at C (negative for Zc > 0).
+ */
+void or_one_electron_primitive(const int* pa, double a, const double* A, const int* pb, double b, const double* B,
+                               double Zc, const double* C, double* out)
+{
+    double p = a + b, P[3];
+    etab E[3];
+    for (int x = 0; x < 3; x++) {
+        P[x] = (a * A[x] + b * B[x]) / p;
+        hermite_E(pa[x], pb[x] + 2, a, b, A[x], B[x], E[x]);
+    }
+    double s1[3], t1[3], sq = sqrt(OR_PI / p);
+    for (int x = 0; x < 3; x++) {
+        int ii = pa[x], jj = pb[x];
+        s1[x] = E[x][ii][jj][0] * sq;
+        double sp2 = E[x][ii][jj + 2][0] * sq;
+        double sm2 = jj >= 2 ? E[x][ii][jj - 2][0] * sq : 0.0;
+        t1[x] = -2.0 * b * b * sp2 + b * (2 * jj + 1) * s1[x] - 0.5 * jj * (jj - 1) * sm2;
+    }
+    out[0] = s1[0] * s1[1] * s1[2];
+    out[1] = t1[0] * s1[1] * s1[2] + s1[0] * t1[1] * s1[2] + s1[0] * s1[1] * t1[2];
+    int L = pa[0] + pa[1] + pa[2] + pb[0] + pb[1] + pb[2];
+    double R[RN][RN][RN];
+    hermite_R(L, p, P[0] - C[0], P[1] - C[1], P[2] - C[2], R);
+    double acc = 0.0;
+    for (int t = 0; t <= pa[0] + pb[0]; t++)
+        for (int u = 0; u <= pa[1] + pb[1]; u++)
+            for (int v = 0; v <= pa[2] + pb[2]; v++) acc += E[0][pa[0]][pb[0]][t] * E[1][pa[1]][pb[1]][u] * E[2][pa[2]][pb[2]][v] * R[t][u][v];
+    out[2] = -Zc * 2.0 * OR_PI / p * acc;
+}
+
 /* ------------------------------------------------------ Two-electron -- */
 /*
  * Contracted shell-quartet block (ab|cd), out[((a*nb+b)*nc+c)*nd+d], by the
