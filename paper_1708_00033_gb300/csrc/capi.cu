@@ -1,0 +1,571 @@
+// C-ABI entry points (include/hf.h): argument checks, device memory, and the
+// order of the setup and Fock-build kernels on the context's stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "eri_common.cuh"
+#include "hf_internal.h"
+#include "setup.cuh"
+
+namespace hf {
+
+static thread_local std::string g_err;
+
+void set_error(int code, const std::string& msg)
+{
+    (void)code;
+    g_err = msg;
+}
+
+int cuda_status(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return HF_E_CUDA;
+}
+
+int DevBuf::alloc(size_t n)
+{
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        g_err = "device allocation of " + std::to_string(n) + " bytes failed";
+        return HF_E_NOMEM;
+    }
+    bytes = n;
+    return HF_OK;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define TRY(x)                       \
+    do {                             \
+        int rc_ = (x);               \
+        if (rc_ != HF_OK) return rc_; \
+    } while (0)
+
+#define KCHK(x)                                                                  \
+    do {                                                                         \
+        if ((x) != 0) return cuda_status(cudaGetLastError(), "kernel launch " #x); \
+    } while (0)
+
+template <typename T>
+int upload(DevBuf& b, const T* host, size_t n, cudaStream_t s)
+{
+    TRY(b.alloc(n * sizeof(T)));
+    if (n) HF_CUDA(cudaMemcpyAsync(b.p, host, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return HF_OK;
+}
+
+size_t next_pow2(size_t n)
+{
+    size_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+int class_index(int X, int Y)
+{
+    for (int c = 0; c < kNumClasses; c++)
+        if (kEriClasses[c].X == X && kEriClasses[c].Y == Y) return c;
+    return -1;
+}
+
+}  // namespace
+
+}  // namespace hf
+
+using namespace hf;
+
+extern "C" {
+
+const char* hf_strerror(int status)
+{
+    switch (status) {
+        case HF_OK: return "success";
+        case HF_E_INVALID: return "invalid argument";
+        case HF_E_UNSUPPORTED: return "unsupported input or device";
+        case HF_E_NOMEM: return "out of memory";
+        case HF_E_CUDA: return "CUDA runtime error";
+        case HF_E_TIMEOUT: return "device wait timed out";
+        case HF_E_NOCONV: return "SCF did not converge";
+        default: return "unknown status";
+    }
+}
+
+const char* hf_last_error(void) { return g_err.c_str(); }
+
+int hf_create(hf_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return fail(HF_E_INVALID, "hf_create: ctx pointer is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(HF_E_UNSUPPORTED, "hf_create: no CUDA device");
+    }
+    if (device < 0 || device >= ndev) return fail(HF_E_INVALID, "hf_create: device index out of range");
+    cudaDeviceProp prop;
+    HF_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(HF_E_UNSUPPORTED, "hf_create: library is built for sm_103a (GB300); device is sm_" +
+                                          std::to_string(prop.major) + std::to_string(prop.minor));
+    DeviceGuard g(device);
+    hf_ctx* c = new hf_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->num_sms = prop.multiProcessorCount;
+    int rc = c->boys64.alloc(sizeof(double) * kBoysRows * kBoysCols);
+    if (rc == HF_OK) rc = c->boys32.alloc(sizeof(float) * kBoysRows * kBoysCols);
+    if (rc == HF_OK && build_boys_tables(c->boys64.as<double>(), c->boys32.as<float>(), c->stream) != 0)
+        rc = cuda_status(cudaGetLastError(), "boys table kernel");
+    if (rc == HF_OK) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = cuda_status(e, "hf_create sync");
+    }
+    if (rc == HF_OK) {
+        for (auto& ev : c->ev) {
+            if (cudaEventCreate(&ev) != cudaSuccess) {
+                rc = cuda_status(cudaGetLastError(), "cudaEventCreate");
+                break;
+            }
+        }
+        c->events_ready = (rc == HF_OK);
+    }
+    if (rc != HF_OK) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return HF_OK;
+}
+
+void hf_destroy(hf_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard g(c->device);
+    if (c->events_ready)
+        for (auto& ev : c->ev)
+            if (ev) cudaEventDestroy(ev);
+    delete c;
+}
+
+}  // extern "C"
+
+static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* basis)
+{
+    hf_ctx* ctx = S->ctx;
+    cudaStream_t st = ctx->stream;
+    hf_system& X = *S;
+    const int na = geom->n_atoms, ns = basis->n_shells;
+    // host bookkeeping of the basis layout (offsets only)
+    std::vector<int> bf0(ns), prim0(ns);
+    int nbf = 0, npr = 0, maxnp = 0;
+    for (int s = 0; s < ns; s++) {
+        bf0[s] = nbf;
+        prim0[s] = npr;
+        nbf += (basis->l[s] + 1) * (basis->l[s] + 2) / 2;
+        npr += basis->nprim[s];
+        maxnp = std::max(maxnp, (int)basis->nprim[s]);
+    }
+    std::vector<double> Zd(na);
+    int nel = 0;
+    for (int a = 0; a < na; a++) {
+        Zd[a] = geom->Z[a];
+        nel += geom->Z[a];
+    }
+    S->n_atoms = na;
+    S->n_shells = ns;
+    S->n_bf = nbf;
+    S->n_electrons = nel;
+    X.maxpp = maxnp * maxnp;
+    TRY(upload(S->sh_l, basis->l, ns, st));
+    TRY(upload(S->sh_atom, basis->atom, ns, st));
+    TRY(upload(S->sh_bf0, bf0.data(), ns, st));
+    TRY(upload(S->sh_nprim, basis->nprim, ns, st));
+    TRY(upload(S->sh_prim0, prim0.data(), ns, st));
+    TRY(upload(S->sh_exp, basis->exps, npr, st));
+    DevBuf coef_in;
+    TRY(upload(coef_in, basis->coefs, npr, st));
+    TRY(upload(S->atom_xyz, geom->xyz, 3 * (size_t)na, st));
+    TRY(upload(S->atom_Z, Zd.data(), na, st));
+    TRY(S->sh_coef.alloc(sizeof(double) * npr));
+    TRY(S->comp_norm.alloc(sizeof(double) * nbf));
+    KCHK(launch_shell_coef(ns, S->sh_l.as<int>(), S->sh_nprim.as<int>(), S->sh_prim0.as<int>(), S->sh_exp.as<double>(),
+                           coef_in.as<double>(), S->sh_coef.as<double>(), st));
+    KCHK(launch_comp_norm(ns, S->sh_l.as<int>(), S->sh_bf0.as<int>(), S->comp_norm.as<double>(), st));
+    const size_t NN = (size_t)nbf * nbf;
+    TRY(S->S.alloc(NN * sizeof(double)));
+    TRY(S->H.alloc(NN * sizeof(double)));
+    KCHK(launch_one_electron(ns, na, nbf, S->sh_l.as<int>(), S->sh_atom.as<int>(), S->sh_bf0.as<int>(),
+                             S->sh_nprim.as<int>(), S->sh_prim0.as<int>(), S->sh_exp.as<double>(),
+                             S->sh_coef.as<double>(), S->atom_xyz.as<double>(), S->atom_Z.as<double>(),
+                             S->comp_norm.as<double>(), ctx->boys64.as<double>(), S->S.as<double>(),
+                             S->H.as<double>(), st));
+    TRY(S->Ebuf.alloc(sizeof(double) * 320));
+    KCHK(launch_nuclear_repulsion(na, S->atom_xyz.as<double>(), S->atom_Z.as<double>(), S->Ebuf.as<double>() + 300,
+                                  st));
+    HF_CUDA(cudaMemcpyAsync(&S->E_nn, S->Ebuf.as<double>() + 300, sizeof(double), cudaMemcpyDeviceToHost, st));
+
+    // ---------------------------------------------------------- shell pairs
+    const long long npairs = (long long)ns * (ns + 1) / 2;
+    if (npairs * (long long)X.maxpp >= (1ll << 31)) return fail(HF_E_UNSUPPORTED, "too many primitive pairs");
+    S->n_pairs_all = (int)npairs;
+    TRY(S->pairs.alloc(sizeof(PairHdr) * npairs));
+    TRY(S->prims64.alloc(sizeof(PrimPair<double>) * npairs * X.maxpp));
+    TRY(S->prims32.alloc(sizeof(PrimPair<float>) * npairs * X.maxpp));
+    TRY(S->pair_class.alloc(sizeof(int) * npairs));
+    KCHK(launch_build_pairs(npairs, X.maxpp, S->sh_l.as<int>(), S->sh_atom.as<int>(), S->sh_bf0.as<int>(),
+                            S->sh_nprim.as<int>(), S->sh_prim0.as<int>(), S->sh_exp.as<double>(),
+                            S->sh_coef.as<double>(), S->atom_xyz.as<double>(), S->pairs.as<PairHdr>(),
+                            S->prims64.p, S->prims32.p, S->pair_class.as<int>(), st));
+    TRY(X.counts.alloc(sizeof(unsigned long long) * 16));
+    HF_CUDA(cudaMemsetAsync(X.counts.p, 0, sizeof(unsigned long long) * 16, st));
+    KCHK(launch_class_count(npairs, S->pair_class.as<int>(), X.counts.as<unsigned long long>(), st));
+    unsigned long long cnt_all[kNumPairClasses];
+    HF_CUDA(cudaMemcpyAsync(cnt_all, X.counts.p, sizeof(cnt_all), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));
+
+    // ------------------------------------------------------ Schwarz bounds
+    TRY(X.Qall.alloc(sizeof(double) * npairs));
+    HF_CUDA(cudaMemsetAsync(X.Qall.p, 0, sizeof(double) * npairs, st));
+    std::vector<DevBuf> ids_all(kNumPairClasses);
+    for (int c = 0; c < kNumPairClasses; c++) {
+        if (!cnt_all[c]) continue;
+        TRY(ids_all[c].alloc(sizeof(int) * cnt_all[c]));
+        HF_CUDA(cudaMemsetAsync(X.counts.as<unsigned long long>() + 8, 0, sizeof(unsigned long long), st));
+        KCHK(launch_class_scatter_all(npairs, S->pair_class.as<int>(), c,
+                                      (unsigned*)(X.counts.as<unsigned long long>() + 8), ids_all[c].as<int>(), st));
+        const int ci = class_index(c, c);
+        SchwarzArgs sa;
+        sa.pairs = S->pairs.as<PairHdr>();
+        sa.prims64 = S->prims64.p;
+        sa.ids = ids_all[c].as<int>();
+        sa.n = (int)cnt_all[c];
+        sa.Q = X.Qall.as<double>();
+        sa.boys64 = ctx->boys64.as<double>();
+        kEriClasses[ci].launch_schwarz(sa, kEriThreads, st);
+        HF_CUDA(cudaGetLastError());
+    }
+    HF_CUDA(cudaMemsetAsync(X.counts.as<unsigned long long>() + 9, 0, sizeof(unsigned long long), st));
+    KCHK(launch_copy_q(npairs, X.Qall.as<double>(), S->pairs.as<PairHdr>(), X.counts.as<unsigned long long>() + 9, st));
+    unsigned long long qbits = 0;
+    HF_CUDA(cudaMemcpyAsync(&qbits, X.counts.as<unsigned long long>() + 9, sizeof(qbits), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));
+    memcpy(&S->Qmax, &qbits, sizeof(double));
+
+    // ------------------------------------- significant pairs, sorted by Q
+    const double tau = S->th.schwarz_tau;
+    for (int c = 0; c < kNumPairClasses; c++) {
+        S->class_count[c] = 0;
+        if (!cnt_all[c]) continue;
+        const size_t npad = next_pow2(cnt_all[c]);
+        DevBuf key, val;
+        TRY(key.alloc(sizeof(double) * npad));
+        TRY(val.alloc(sizeof(int) * npad));
+        HF_CUDA(cudaMemsetAsync(X.counts.as<unsigned long long>() + 10, 0, sizeof(unsigned long long), st));
+        KCHK(launch_class_scatter_sig(npairs, S->pair_class.as<int>(), X.Qall.as<double>(), c, S->Qmax, tau,
+                                      (unsigned*)(X.counts.as<unsigned long long>() + 10), key.as<double>(),
+                                      val.as<int>(), st));
+        unsigned nsig = 0;
+        HF_CUDA(cudaMemcpyAsync(&nsig, X.counts.as<unsigned long long>() + 10, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                st));
+        HF_CUDA(cudaStreamSynchronize(st));
+        S->class_count[c] = (int)nsig;
+        if (!nsig) continue;
+        const size_t npad2 = next_pow2(nsig);
+        KCHK(bitonic_sort_desc(key.as<double>(), val.as<int>(), (int)nsig, (int)npad2, st));
+        TRY(S->class_ids[c].alloc(sizeof(int) * nsig));
+        TRY(X.class_q[c].alloc(sizeof(double) * nsig));
+        HF_CUDA(cudaMemcpyAsync(S->class_ids[c].p, val.p, sizeof(int) * nsig, cudaMemcpyDeviceToDevice, st));
+        HF_CUDA(cudaMemcpyAsync(X.class_q[c].p, key.p, sizeof(double) * nsig, cudaMemcpyDeviceToDevice, st));
+        HF_CUDA(cudaStreamSynchronize(st));
+    }
+
+    // ------------------------------------------------- quartet schedule
+    S->quartets_total = 0;
+    for (int ci = 0; ci < kNumClasses; ci++) {
+        const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
+        auto& pl = S->plan[ci];
+        pl.n_unscreened = (Xc == Yc) ? (long long)cnt_all[Xc] * (cnt_all[Xc] + 1) / 2
+                                     : (long long)cnt_all[Xc] * (long long)cnt_all[Yc];
+        S->quartets_total += pl.n_unscreened;
+        pl.n64 = pl.n32 = 0;
+        const int nb = S->class_count[Xc], nk = S->class_count[Yc];
+        if (!nb || !nk) continue;
+        DevBuf c64, c32;
+        TRY(c64.alloc(sizeof(long long) * nb));
+        TRY(c32.alloc(sizeof(long long) * nb));
+        TRY(pl.kstart32.alloc(sizeof(int) * nb));
+        TRY(pl.offsets64.alloc(sizeof(long long) * (nb + 1)));
+        TRY(pl.offsets32.alloc(sizeof(long long) * (nb + 1)));
+        KCHK(launch_ket_counts(nb, X.class_q[Xc].as<double>(), nk, X.class_q[Yc].as<double>(), Xc == Yc, tau,
+                               S->th.fp32_cutoff, c64.as<long long>(), c32.as<long long>(), pl.kstart32.as<int>(), st));
+        KCHK(launch_scan(nb, c64.as<long long>(), pl.offsets64.as<long long>(), st));
+        KCHK(launch_scan(nb, c32.as<long long>(), pl.offsets32.as<long long>(), st));
+        HF_CUDA(cudaMemcpyAsync(&pl.n64, pl.offsets64.as<long long>() + nb, sizeof(long long), cudaMemcpyDeviceToHost,
+                                st));
+        HF_CUDA(cudaMemcpyAsync(&pl.n32, pl.offsets32.as<long long>() + nb, sizeof(long long), cudaMemcpyDeviceToHost,
+                                st));
+        HF_CUDA(cudaStreamSynchronize(st));
+    }
+
+    // ------------------------------------------------------- work buffers
+    TRY(S->P64.alloc(NN * sizeof(double)));
+    if (S->th.fp32_cutoff > 0.0) TRY(S->P32.alloc(NN * sizeof(float)));
+    TRY(S->Jt.alloc(NN * sizeof(double)));
+    TRY(S->Kt.alloc(NN * sizeof(double)));
+    TRY(S->F.alloc(NN * sizeof(double)));
+    TRY(X.staging_P.alloc(NN * sizeof(double)));
+    TRY(X.staging_out.alloc(2 * NN * sizeof(double)));
+    TRY(X.bad.alloc(sizeof(int)));
+    HF_CUDA(cudaStreamSynchronize(st));
+    HF_CUDA(cudaGetLastError());
+    return HF_OK;
+}
+
+static int check_geometry_basis(const hf_geometry* g, const hf_basis* b, const hf_thresholds* th)
+{
+    if (!g || !b) return fail(HF_E_INVALID, "geometry or basis is NULL");
+    if (g->n_atoms < 1 || !g->Z || !g->xyz) return fail(HF_E_INVALID, "geometry: empty or NULL arrays");
+    if (b->n_shells < 1 || !b->atom || !b->l || !b->nprim || !b->exps || !b->coefs)
+        return fail(HF_E_INVALID, "basis: empty or NULL arrays");
+    for (int a = 0; a < g->n_atoms; a++) {
+        if (g->Z[a] < 0) return fail(HF_E_INVALID, "geometry: negative nuclear charge");
+        for (int x = 0; x < 3; x++)
+            if (!isfinite(g->xyz[3 * a + x])) return fail(HF_E_INVALID, "geometry: non-finite coordinate");
+    }
+    long long np = 0;
+    for (int s = 0; s < b->n_shells; s++) {
+        if (b->atom[s] < 0 || b->atom[s] >= g->n_atoms) return fail(HF_E_INVALID, "basis: atom index out of range");
+        if (b->l[s] < 0) return fail(HF_E_INVALID, "basis: negative angular momentum");
+        if (b->l[s] > kMaxL) return fail(HF_E_UNSUPPORTED, "basis: l > 2 is not supported");
+        if (b->nprim[s] < 1) return fail(HF_E_INVALID, "basis: shell without primitives");
+        if (b->nprim[s] > kMaxPrim) return fail(HF_E_UNSUPPORTED, "basis: more than 8 primitives in a shell");
+        np += b->nprim[s];
+    }
+    for (long long k = 0; k < np; k++) {
+        if (!(b->exps[k] > 0.0) || !isfinite(b->exps[k])) return fail(HF_E_INVALID, "basis: exponent not positive");
+        if (!isfinite(b->coefs[k])) return fail(HF_E_INVALID, "basis: non-finite coefficient");
+    }
+    if (th) {
+        if (!(th->schwarz_tau >= 0.0) || !(th->fp32_cutoff >= 0.0)) return fail(HF_E_INVALID, "thresholds: negative");
+        if (th->prim_tau != 0.0) return fail(HF_E_UNSUPPORTED, "thresholds: prim_tau must be 0");
+    }
+    return HF_OK;
+}
+
+extern "C" {
+
+int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis, const hf_thresholds* th,
+                     hf_system** out)
+{
+    if (!ctx || !out) return fail(HF_E_INVALID, "hf_system_create: NULL ctx or output pointer");
+    *out = nullptr;
+    TRY(check_geometry_basis(geom, basis, th));
+    DeviceGuard g(ctx->device);
+    hf_system* S = new hf_system();
+    S->ctx = ctx;
+    if (th) S->th = *th;
+    int rc = system_setup(S, geom, basis);
+    if (rc != HF_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        delete S;
+        return rc;
+    }
+    *out = S;
+    return HF_OK;
+}
+
+void hf_system_destroy(hf_system* S)
+{
+    if (!S) return;
+    DeviceGuard g(S->ctx->device);
+    cudaStreamSynchronize(S->ctx->stream);
+    delete S;
+}
+
+int hf_system_get_info(const hf_system* S, hf_system_info* info)
+{
+    if (!S || !info) return fail(HF_E_INVALID, "hf_system_get_info: NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->n_atoms = S->n_atoms;
+    info->n_shells = S->n_shells;
+    info->n_bf = S->n_bf;
+    info->n_electrons = S->n_electrons;
+    info->n_pairs = S->n_pairs_all;
+    for (int c = 0; c < kNumPairClasses; c++) info->n_significant_pairs += S->class_count[c];
+    info->quartets_unscreened = S->quartets_total;
+    for (int c = 0; c < kNumClasses; c++) {
+        info->quartets_fp64 += S->plan[c].n64;
+        info->quartets_fp32 += S->plan[c].n32;
+    }
+    info->E_nn = S->E_nn;
+    info->Q_max = S->Qmax;
+    long long bytes = 0;
+    const DevBuf* bufs[] = {&S->sh_l, &S->sh_atom, &S->sh_bf0, &S->sh_nprim, &S->sh_prim0, &S->sh_exp, &S->sh_coef,
+                            &S->atom_xyz, &S->atom_Z, &S->comp_norm, &S->pairs, &S->prims64, &S->prims32,
+                            &S->pair_class, &S->S, &S->H, &S->P64, &S->P32, &S->Jt, &S->Kt, &S->F, &S->Ebuf,
+                            &S->Qall, &S->staging_P, &S->staging_out};
+    for (auto* b : bufs) bytes += b->bytes;
+    for (int c = 0; c < kNumPairClasses; c++) bytes += S->class_ids[c].bytes + S->class_q[c].bytes;
+    for (int c = 0; c < kNumClasses; c++)
+        bytes += S->plan[c].offsets64.bytes + S->plan[c].offsets32.bytes + S->plan[c].kstart32.bytes;
+    info->device_bytes = bytes;
+    return HF_OK;
+}
+
+int hf_one_electron(hf_system* S, double* Sout, double* Hout, int flags)
+{
+    if (!S) return fail(HF_E_INVALID, "hf_one_electron: NULL system");
+    DeviceGuard g(S->ctx->device);
+    const size_t bytes = (size_t)S->n_bf * S->n_bf * sizeof(double);
+    const cudaMemcpyKind kind = (flags & HF_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t st = S->ctx->stream;
+    if (Sout) HF_CUDA(cudaMemcpyAsync(Sout, S->S.p, bytes, kind, st));
+    if (Hout) HF_CUDA(cudaMemcpyAsync(Hout, S->H.p, bytes, kind, st));
+    HF_CUDA(cudaStreamSynchronize(st));
+    return HF_OK;
+}
+
+int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
+                  int flags)
+{
+    if (!S || !P) return fail(HF_E_INVALID, "hf_fock_build: NULL system or density");
+    DeviceGuard g(S->ctx->device);
+    hf_ctx* ctx = S->ctx;
+    hf_system& X = *S;
+    cudaStream_t st = ctx->stream;
+    const int N = S->n_bf;
+    const size_t NN = (size_t)N * N;
+    const bool dev = (flags & HF_PTR_DEVICE) != 0;
+    const bool timing = (flags & HF_TIMING) != 0 && stats;
+    // 1. density in, check, raw-normalised copies
+    const double* dP = P;
+    if (!dev) {
+        HF_CUDA(cudaMemcpyAsync(X.staging_P.p, P, NN * sizeof(double), cudaMemcpyHostToDevice, st));
+        dP = X.staging_P.as<double>();
+    }
+    if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses], st));
+    HF_CUDA(cudaMemsetAsync(X.bad.p, 0, sizeof(int), st));
+    KCHK(launch_scale_density(N, dP, S->comp_norm.as<double>(), S->P64.as<double>(),
+                              S->P32.p ? S->P32.as<float>() : nullptr, X.bad.as<int>(), st));
+    int bad = 0;
+    HF_CUDA(cudaMemcpyAsync(&bad, X.bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));
+    if (bad) return fail(HF_E_INVALID, "hf_fock_build: density is not finite or not symmetric");
+    // 2. ERI + digestion, one launch per class and precision
+    HF_CUDA(cudaMemsetAsync(S->Jt.p, 0, NN * sizeof(double), st));
+    HF_CUDA(cudaMemsetAsync(S->Kt.p, 0, NN * sizeof(double), st));
+    if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 1], st));
+    EriArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pairs = S->pairs.as<PairHdr>();
+    a.prims64 = S->prims64.p;
+    a.prims32 = S->prims32.p;
+    a.N = N;
+    a.P64 = S->P64.as<double>();
+    a.P32 = S->P32.p ? S->P32.as<float>() : nullptr;
+    a.Jt = S->Jt.as<double>();
+    a.Kt = S->Kt.as<double>();
+    a.boys64 = ctx->boys64.as<double>();
+    a.boys32 = ctx->boys32.as<float>();
+    for (int ci = 0; ci < kNumClasses; ci++) {
+        const auto& pl = S->plan[ci];
+        const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
+        a.bra = S->class_ids[Xc].as<int>();
+        a.ket = S->class_ids[Yc].as<int>();
+        a.n_bra = S->class_count[Xc];
+        a.same = Xc == Yc;
+        for (int prec = 0; prec < 2; prec++) {
+            const long long n = prec ? pl.n32 : pl.n64;
+            if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * ci + 2 * prec], st));
+            if (n > 0) {
+                a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
+                a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
+                a.n_quartets = n;
+                const long long blocks = (n + kEriThreads - 1) / kEriThreads;
+                const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
+                kEriClasses[ci].launch(a, prec, grid, kEriThreads, st);
+                HF_CUDA(cudaGetLastError());
+            }
+            if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * ci + 2 * prec + 1], st));
+        }
+    }
+    if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 2], st));
+    // 3. symmetrise and assemble
+    double* dF = dev && F ? F : S->F.as<double>();
+    double* dJ = dev ? J : (J ? X.staging_out.as<double>() : nullptr);
+    double* dK = dev ? K : (K ? X.staging_out.as<double>() + NN : nullptr);
+    KCHK(launch_assemble(N, S->Jt.as<double>(), S->Kt.as<double>(), S->comp_norm.as<double>(), S->H.as<double>(), dJ,
+                         dK, dF, st));
+    if (E_elec) KCHK(launch_energy(N, dP, S->H.as<double>(), dF, S->Ebuf.as<double>(), S->Ebuf.as<double>() + 256, st));
+    if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 3], st));
+    if (!dev) {
+        if (F) HF_CUDA(cudaMemcpyAsync(F, dF, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (J) HF_CUDA(cudaMemcpyAsync(J, dJ, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (K) HF_CUDA(cudaMemcpyAsync(K, dK, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (E_elec) HF_CUDA(cudaMemcpyAsync(E_elec, S->Ebuf.as<double>() + 256, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));
+    HF_CUDA(cudaGetLastError());
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->quartets_unscreened = S->quartets_total;
+        const double pq = (double)X.maxpp * (double)X.maxpp;  // primitive quartets per shell quartet (upper bound)
+        for (int ci = 0; ci < kNumClasses; ci++) {
+            const auto& pl = S->plan[ci];
+            stats->class_quartets_fp64[ci] = pl.n64;
+            stats->class_quartets_fp32[ci] = pl.n32;
+            stats->quartets_fp64 += pl.n64;
+            stats->quartets_fp32 += pl.n32;
+            const double per = kEriClasses[ci].prim_flops * pq + kEriClasses[ci].cont_flops;
+            stats->flops_fp64 += per * (double)pl.n64;
+            stats->flops_fp32 += per * (double)pl.n32;
+            if (timing) {
+                cudaEventElapsedTime(&stats->ms_class_fp64[ci], ctx->ev[4 * ci], ctx->ev[4 * ci + 1]);
+                cudaEventElapsedTime(&stats->ms_class_fp32[ci], ctx->ev[4 * ci + 2], ctx->ev[4 * ci + 3]);
+            }
+        }
+        if (timing) {
+            cudaEventElapsedTime(&stats->ms_eri, ctx->ev[4 * kNumClasses + 1], ctx->ev[4 * kNumClasses + 2]);
+            cudaEventElapsedTime(&stats->ms_total, ctx->ev[4 * kNumClasses], ctx->ev[4 * kNumClasses + 3]);
+        }
+    }
+    return HF_OK;
+}
+
+}  // extern "C"

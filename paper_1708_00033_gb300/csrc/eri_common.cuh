@@ -1,0 +1,176 @@
+// Device-side building blocks shared by the generated ERI class kernels.
+//
+// Shell pairs (Algorithm 1's (i, j) index; Section 4.1's shell footnote) are
+// stored once per significant unordered pair, oriented so that l_A >= l_B,
+// with one record per primitive pair.  Quartets of one angular class are the
+// pairs (bra b, ket k) of two Schwarz-sorted pair lists; bra b owns the ket
+// prefix [kstart[b], kstart[b] + offsets[b+1] - offsets[b]), which is how the
+// screening of Algorithm 1 (schwartz(i,j,k,l)) becomes a per-bra cut on a list
+// sorted by Q_kl.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hf_internal.h"
+
+namespace hf {
+
+template <typename real>
+struct PrimPair {
+    real p;              // a + b
+    real Px, Py, Pz;     // (a A + b B) / p
+    real PAx, PAy, PAz;  // P - A
+    real K;              // c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p
+    real oo2p;           // 1 / (2p)
+};
+
+// Boys table: rows T_k = k / 32 for k = 0..kBoysRows-1 (T < 60); columns
+// F_0..F_14 at T_k and exp(-T_k) in the last column.
+constexpr int kBoysRows = 1921;
+constexpr int kBoysCols = 16;
+constexpr int kBoysExpCol = 15;
+constexpr double kBoysTmax = 60.0;
+
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+
+// F_m(T), m = 0..L.  Below T = 60: seven-term Taylor expansion about the
+// nearest grid point (|T - T_k| <= 1/64, truncation < 5e-17 relative), using
+// dF_m/dT = -F_{m+1}; for L >= 2 only F_L is expanded and the rest follow by
+// the downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1), with exp(-T)
+// itself expanded about T_k.  Above: F_0 = sqrt(pi/T)/2 and the upward
+// recursion F_{m+1} = (2m+1) F_m / (2T) (exp(-T) < 1e-26 is dropped).
+template <int L>
+__device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double* F)
+{
+    if (T < kBoysTmax) {
+        const int k = __double2int_rn(T * 32.0);
+        const double d = k * (1.0 / 32.0) - T;
+        const double* __restrict__ r = tab + k * kBoysCols;
+        const double d2 = d * 0.5, d3 = d * (1.0 / 3.0), d4 = d * 0.25, d5 = d * 0.2, d6 = d * (1.0 / 6.0);
+        if constexpr (L <= 1) {
+#pragma unroll
+            for (int m = 0; m <= L; m++)
+                F[m] = r[m] + d * (r[m + 1] + d2 * (r[m + 2] + d3 * (r[m + 3] + d4 * (r[m + 4] + d5 * (r[m + 5] + d6 * r[m + 6])))));
+        } else {
+            F[L] = r[L] + d * (r[L + 1] + d2 * (r[L + 2] + d3 * (r[L + 3] + d4 * (r[L + 4] + d5 * (r[L + 5] + d6 * r[L + 6])))));
+            const double d7 = d * (1.0 / 7.0);
+            const double e = r[kBoysExpCol] * (1.0 + d * (1.0 + d2 * (1.0 + d3 * (1.0 + d4 * (1.0 + d5 * (1.0 + d6 * (1.0 + d7)))))));
+            const double t2 = T + T;
+#pragma unroll
+            for (int m = L - 1; m >= 0; m--) F[m] = (t2 * F[m + 1] + e) * (1.0 / (2 * m + 1));
+        }
+    } else {
+        const double rs = rsqrt(T);
+        F[0] = 0.88622692545275801365 * rs;
+        if constexpr (L > 0) {
+            const double h = 0.5 * rs * rs;
+#pragma unroll
+            for (int m = 0; m < L; m++) F[m + 1] = F[m] * ((2 * m + 1) * h);
+        }
+    }
+}
+
+// Single-precision variant for the mixed path: four Taylor terms (truncation
+// < 3e-9 relative), same recursions.
+template <int L>
+__device__ __forceinline__ void boys_eval(float T, const float* __restrict__ tab, float* F)
+{
+    if (T < (float)kBoysTmax) {
+        const int k = __float2int_rn(T * 32.0f);
+        const float d = k * (1.0f / 32.0f) - T;
+        const float* __restrict__ r = tab + k * kBoysCols;
+        const float d2 = d * 0.5f, d3 = d * (1.0f / 3.0f);
+        if constexpr (L <= 1) {
+#pragma unroll
+            for (int m = 0; m <= L; m++) F[m] = r[m] + d * (r[m + 1] + d2 * (r[m + 2] + d3 * r[m + 3]));
+        } else {
+            F[L] = r[L] + d * (r[L + 1] + d2 * (r[L + 2] + d3 * r[L + 3]));
+            const float e = r[kBoysExpCol] * (1.0f + d * (1.0f + d2 * (1.0f + d3 * (1.0f + d * 0.25f))));
+            const float t2 = T + T;
+#pragma unroll
+            for (int m = L - 1; m >= 0; m--) F[m] = (t2 * F[m + 1] + e) * (1.0f / (2 * m + 1));
+        }
+    } else {
+        const float rs = rsqrtf(T);
+        F[0] = 0.886226925f * rs;
+        if constexpr (L > 0) {
+            const float h = 0.5f * rs * rs;
+#pragma unroll
+            for (int m = 0; m < L; m++) F[m + 1] = F[m] * ((2 * m + 1) * h);
+        }
+    }
+}
+
+template <typename real, int L>
+__device__ __forceinline__ void boys(real T, const real* __restrict__ tab, real* F)
+{
+    boys_eval<L>(T, tab, F);
+}
+
+__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
+
+// Largest b in [0, n) with off[b] <= q (off is non-decreasing, off[0] = 0).
+__device__ __forceinline__ int find_bra(const long long* __restrict__ off, int n, long long q)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= q)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kEriThreads = 128;
+
+}  // namespace hf
+
+// Kernels and host launchers of one class.  The digestion weight of a unique
+// shell quartet is f = 1/((1+d_AB)(1+d_CD)(1+d_AB,CD)).
+#define ERI_CLASS_KERNELS(NAME, X, Y)                                                                        \
+    template <typename real>                                                                                 \
+    __global__ void __launch_bounds__(kEriThreads) k_eri_##NAME(const EriArgs a)                            \
+    {                                                                                                        \
+        const PrimPair<real>* prims = (const PrimPair<real>*)(sizeof(real) == 8 ? a.prims64 : a.prims32);   \
+        const real* P = (const real*)(sizeof(real) == 8 ? (const void*)a.P64 : (const void*)a.P32);                                  \
+        const real* bt = (const real*)(sizeof(real) == 8 ? (const void*)a.boys64 : (const void*)a.boys32);  \
+        const long long stride = (long long)gridDim.x * blockDim.x;                                          \
+        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_quartets; q += stride) { \
+            const int b = find_bra(a.offsets, a.n_bra, q);                                                   \
+            const int k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                            \
+            const PairHdr hb = a.pairs[a.bra[b]];                                                            \
+            const PairHdr hk = a.pairs[a.ket[k]];                                                            \
+            double f = 1.0;                                                                                  \
+            if (hb.A == hb.B) f *= 0.5;                                                                      \
+            if (hk.A == hk.B) f *= 0.5;                                                                      \
+            if (a.same && b == k) f *= 0.5;                                                                  \
+            quartet_##NAME<real>(hb, hk, prims, bt, P, a.N, f, a.Jt, a.Kt, nullptr);                         \
+        }                                                                                                    \
+    }                                                                                                        \
+    void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s)              \
+    {                                                                                                        \
+        if (use_f32)                                                                                         \
+            k_eri_##NAME<float><<<grid, block, 0, s>>>(a);                                                   \
+        else                                                                                                 \
+            k_eri_##NAME<double><<<grid, block, 0, s>>>(a);                                                  \
+    }
+
+// Schwarz bounds of the pairs of a diagonal class: Q = sqrt(max |(ab|ab)|).
+#define SCHWARZ_KERNEL(NAME)                                                                                 \
+    __global__ void __launch_bounds__(kEriThreads) k_schwarz_##NAME(const SchwarzArgs a)                    \
+    {                                                                                                        \
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;                                                 \
+        if (t >= a.n) return;                                                                                \
+        const int pid = a.ids[t];                                                                            \
+        const PairHdr h = a.pairs[pid];                                                                      \
+        double qm = 0.0;                                                                                     \
+        quartet_##NAME<double>(h, h, (const PrimPair<double>*)a.prims64, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm);          \
+        a.Q[pid] = sqrt(qm);                                                                                 \
+    }                                                                                                        \
+    void launch_schwarz_##NAME(const SchwarzArgs& a, int block, cudaStream_t s)                             \
+    {                                                                                                        \
+        if (a.n > 0) k_schwarz_##NAME<<<(a.n + block - 1) / block, block, 0, s>>>(a);                        \
+    }

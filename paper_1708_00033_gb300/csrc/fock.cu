@@ -1,0 +1,99 @@
+// Fock-matrix assembly around the ERI kernels (the 2e-Fock reduction and
+// flush of Algorithms 1-3, ddi_gsumf + buffer flushes):
+//   P' = n P n             density in the library's raw component normalisation
+//                          (n = Cartesian component factors), with a finiteness
+//                          and symmetry check of P;
+//   J = n (Jt + Jt^T) n / 2, K = n (Kt + Kt^T) n / 2, F = H + J - K/2;
+//   E_elec = 1/2 sum P (H + F), reduced in a fixed order.
+#include <math.h>
+
+#include "eri_common.cuh"
+#include "setup.cuh"
+
+namespace hf {
+
+__global__ void k_scale_density(int N, const double* __restrict__ P, const double* __restrict__ n,
+                                double* __restrict__ P64, float* __restrict__ P32, int* __restrict__ bad)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)N * N) return;
+    const int i = (int)(t / N), j = (int)(t % N);
+    const double v = P[t], w = P[(size_t)j * N + i];
+    if (!isfinite(v) || fabs(v - w) > 1e-12 * fmax(1.0, fabs(v))) atomicOr(bad, 1);
+    const double s = n[i] * n[j] * v;
+    P64[t] = s;
+    if (P32) P32[t] = (float)s;
+}
+
+__global__ void k_assemble(int N, const double* __restrict__ Jt, const double* __restrict__ Kt,
+                           const double* __restrict__ n, const double* __restrict__ H, double* __restrict__ J,
+                           double* __restrict__ K, double* __restrict__ F)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)N * N) return;
+    const int i = (int)(t / N), j = (int)(t % N);
+    const size_t tt = (size_t)j * N + i;
+    const double s = 0.5 * n[i] * n[j];
+    const double jv = s * (Jt[t] + Jt[tt]);
+    const double kv = s * (Kt[t] + Kt[tt]);
+    if (J) J[t] = jv;
+    if (K) K[t] = kv;
+    if (F) F[t] = H[t] + jv - 0.5 * kv;
+}
+
+__global__ void k_energy_partial(long long n, const double* __restrict__ P, const double* __restrict__ H,
+                                 const double* __restrict__ F, double* __restrict__ partial)
+{
+    __shared__ double sm[256];
+    double e = 0.0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        e += P[t] * (H[t] + F[t]);
+    sm[threadIdx.x] = e;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+__global__ void k_energy_final(int nb, const double* __restrict__ partial, double* __restrict__ out)
+{
+    __shared__ double sm[256];
+    double e = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) e += partial[b];
+    sm[threadIdx.x] = e;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = 0.5 * sm[0];
+}
+
+int launch_scale_density(int N, const double* P, const double* comp_norm, double* P64, float* P32, int* bad,
+                         cudaStream_t s)
+{
+    const long long n = (long long)N * N;
+    if (n > 0) k_scale_density<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(N, P, comp_norm, P64, P32, bad);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_assemble(int N, const double* Jt, const double* Kt, const double* comp_norm, const double* H, double* J,
+                    double* K, double* F, cudaStream_t s)
+{
+    const long long n = (long long)N * N;
+    if (n > 0) k_assemble<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(N, Jt, Kt, comp_norm, H, J, K, F);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// partial must hold 256 doubles
+int launch_energy(int N, const double* P, const double* H, const double* F, double* partial, double* out,
+                  cudaStream_t s)
+{
+    k_energy_partial<<<256, 256, 0, s>>>((long long)N * N, P, H, F, partial);
+    k_energy_final<<<1, 256, 0, s>>>(256, partial, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace hf

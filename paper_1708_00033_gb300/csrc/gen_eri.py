@@ -1,0 +1,474 @@
+"""Generator of the per-angular-class ERI + J/K digestion kernels.
+
+For every shell-quartet class (ab|cd) with l_a >= l_b, l_c >= l_d, l <= 2 and
+bra pair class >= ket pair class (21 classes) this emits straight-line CUDA:
+
+  per primitive quartet
+    Boys F_m(T), m <= L = l_a+l_b+l_c+l_d, from a Taylor table (eri_common.cuh);
+    [00|00]^(m) = prefactor * F_m(T);
+    Obara-Saika vertical recurrence on electron 1
+      [e+1_i 0|00]^(m) = PA_i [e0|00]^(m) + WP_i [e0|00]^(m+1)
+                         + e_i/(2p) ([e-1_i 0|00]^(m) - rho/p [e-1_i 0|00]^(m+1))
+    and on electron 2
+      [e0|f+1_i 0]^(m) = QC_i [e0|f0]^(m) + WQ_i [e0|f0]^(m+1)
+                         + f_i/(2q) ([e0|f-1_i 0]^(m) - rho/q [e0|f-1_i 0]^(m+1))
+                         + e_i/(2(p+q)) [e-1_i 0|f0]^(m+1)
+    up to the targets [e0|f0]^(0), l_a <= |e| <= l_a+l_b, l_c <= |f| <= l_c+l_d,
+    accumulated over primitives (contraction before the horizontal step);
+  per contracted quartet
+    Head-Gordon-Pople horizontal recurrence (a b+1_i| = (a+1_i b| + AB_i (a b|,
+    and the same on the ket with CD = C - D;
+    digestion of the block X into the six Fock updates of Eq. 1a-1f with the
+    unique-quartet weight f:  Jt_AB += 4f X.P_CD, Jt_CD += 4f X.P_AB,
+    Kt_AC += 2f X.P_BD, Kt_BD += 2f X.P_AC, Kt_AD += 2f X.P_BC, Kt_BC += 2f X.P_AD,
+    flushed with FP64 atomics (red.global.add.f64).
+
+Only intermediates reachable from the targets are emitted, so each class does
+the minimum recurrence work for its angular momenta.  The generator also
+counts the floating-point operations per primitive quartet and per
+contracted quartet; the library reports algorithmic FLOPs from these counts.
+
+The emitted code is a template on the arithmetic type; it is instantiated for
+double (the FP64 path) and float (small quartets of the mixed path, which
+still accumulate into FP64 Fock matrices).
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+
+CART = {L: [(x, y, L - x - y) for x in range(L, -1, -1) for y in range(L - x, -1, -1)] for L in range(9)}
+PAIR_CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+PAIR_NAMES = ["ss", "ps", "pp", "ds", "dp", "dd"]
+AX = "xyz"
+
+
+def classes():
+    out = []
+    for X in range(len(PAIR_CLASSES)):
+        for Y in range(X + 1):
+            out.append((X, Y))
+    return out
+
+
+def cidx(t):
+    return CART[sum(t)].index(t)
+
+
+def tstr(t):
+    return f"{sum(t)}_{cidx(t)}"
+
+
+def sub(t, i, k=1):
+    l = list(t)
+    l[i] -= k
+    return tuple(l)
+
+
+def add(t, i, k=1):
+    l = list(t)
+    l[i] += k
+    return tuple(l)
+
+
+def first_nz(t):
+    for i in range(3):
+        if t[i] > 0:
+            return i
+    return -1
+
+
+Z3 = (0, 0, 0)
+
+
+class Counter:
+    def __init__(self):
+        self.prim = 0      # flops per primitive quartet (VRR + accumulation, excluding setup/Boys)
+        self.cont = 0      # flops per contracted quartet (HRR + digestion)
+
+
+def vname(e, f, m):
+    return f"v{tstr(e)}_{tstr(f)}_{m}"
+
+
+def gen_vrr(la, lb, lc, ld, cnt):
+    """Return (lines, used-coefficient set) for the VRR of one primitive quartet."""
+    L = la + lb + lc + ld
+    targets = [(e, f, 0) for le in range(la, la + lb + 1) for e in CART[le]
+               for lf in range(lc, lc + ld + 1) for f in CART[lf]]
+    recipe = {}
+
+    def need(node):
+        if node in recipe:
+            return
+        e, f, m = node
+        if e == Z3 and f == Z3:
+            recipe[node] = ("base",)
+            return
+        if f == Z3:
+            i = first_nz(e)
+            e1 = sub(e, i)
+            deps = [(e1, Z3, m), (e1, Z3, m + 1)]
+            if e[i] >= 2:
+                e2 = sub(e, i, 2)
+                deps += [(e2, Z3, m), (e2, Z3, m + 1)]
+            recipe[node] = ("e1", i, deps)
+        else:
+            i = first_nz(f)
+            f1 = sub(f, i)
+            deps = [(e, f1, m), (e, f1, m + 1)]
+            if f[i] >= 2:
+                f2 = sub(f, i, 2)
+                deps += [(e, f2, m), (e, f2, m + 1)]
+            if e[i] >= 1:
+                deps += [(sub(e, i), f1, m + 1)]
+            recipe[node] = ("e2", i, deps)
+        for d in recipe[node][-1] if recipe[node][0] != "base" else []:
+            need(d)
+
+    for t in targets:
+        need(t)
+    order = sorted(recipe.keys(), key=lambda n: (sum(n[0]) + sum(n[1]), sum(n[1]), -n[2]))
+    used = set()
+    lines = []
+    for node in order:
+        e, f, m = node
+        r = recipe[node]
+        nm = vname(e, f, m)
+        if r[0] == "base":
+            lines.append(f"const real {nm} = pref * F[{m}];")
+            cnt.prim += 1
+            continue
+        i = r[1]
+        a = AX[i]
+        if r[0] == "e1":
+            e1 = sub(e, i)
+            expr = f"PA{a} * {vname(e1, Z3, m)} + WP{a} * {vname(e1, Z3, m + 1)}"
+            used.update({f"PA{a}", f"WP{a}"})
+            cnt.prim += 3
+            if e[i] >= 2:
+                e2 = sub(e, i, 2)
+                k = e[i] - 1
+                expr += f" + o2p_{k} * ({vname(e2, Z3, m)} - rho_p * {vname(e2, Z3, m + 1)})"
+                used.update({f"o2p_{k}", "rho_p"})
+                cnt.prim += 4
+            lines.append(f"const real {nm} = {expr};")
+        else:
+            f1 = sub(f, i)
+            expr = f"QC{a} * {vname(e, f1, m)} + WQ{a} * {vname(e, f1, m + 1)}"
+            used.update({f"QC{a}", f"WQ{a}"})
+            cnt.prim += 3
+            if f[i] >= 2:
+                f2 = sub(f, i, 2)
+                k = f[i] - 1
+                expr += f" + o2q_{k} * ({vname(e, f2, m)} - rho_q * {vname(e, f2, m + 1)})"
+                used.update({f"o2q_{k}", "rho_q"})
+                cnt.prim += 4
+            if e[i] >= 1:
+                k = e[i]
+                expr += f" + o2pq_{k} * {vname(sub(e, i), f1, m + 1)}"
+                used.add(f"o2pq_{k}")
+                cnt.prim += 2
+            lines.append(f"const real {nm} = {expr};")
+    acc = []
+    for (e, f, m) in targets:
+        acc.append(f"acc{tstr(e)}_{tstr(f)} += {vname(e, f, 0)};")
+        cnt.prim += 1
+    return lines, acc, used, targets
+
+
+def gen_setup(L, used, cnt):
+    """Per-primitive-quartet quantities; returns lines (flop counts approximate the emitted ops)."""
+    lines = [
+        "const real s = bp.p + kp.p;",
+        "const real rs = rsq(s);",
+        "const real inv = rs * rs;",
+        "const real PQx = bp.Px - kp.Px, PQy = bp.Py - kp.Py, PQz = bp.Pz - kp.Pz;",
+        "const real rho = bp.p * kp.p * inv;",
+        "const real T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);",
+        "const real pref = bK * kp.K * rs;",
+        f"real F[{L + 1}];",
+        f"boys<real, {L}>(T, boys_tab, F);",
+    ]
+    cnt_setup = 1 + 8 + 1 + 3 + 2 + 6 + 2
+    if L > 0:
+        lines += ["const real rho_p = kp.p * inv;", "const real rho_q = bp.p * inv;"]
+        cnt_setup += 2
+        for a in AX:
+            if f"WP{a}" in used:
+                lines.append(f"const real WP{a} = -rho_p * PQ{a};")
+                cnt_setup += 1
+            if f"WQ{a}" in used:
+                lines.append(f"const real WQ{a} = rho_q * PQ{a};")
+                cnt_setup += 1
+        for k in range(1, 5):
+            if f"o2p_{k}" in used:
+                lines.append(f"const real o2p_{k} = real({k}) * bo2p;")
+                cnt_setup += 1
+            if f"o2q_{k}" in used:
+                lines.append(f"const real o2q_{k} = real({k}) * kp.oo2p;")
+                cnt_setup += 1
+        if any(u.startswith("o2pq_") for u in used):
+            lines.append("const real o2pq_1 = real(0.5) * inv;")
+            cnt_setup += 1
+            for k in range(2, 5):
+                if f"o2pq_{k}" in used:
+                    lines.append(f"const real o2pq_{k} = real({k}) * o2pq_1;")
+                    cnt_setup += 1
+        for a in AX:
+            if f"QC{a}" in used:
+                lines.append(f"const real QC{a} = kp.PA{a};")
+    return lines, cnt_setup
+
+
+def boys_flops(L):
+    if L <= 1:
+        return 5 + 7 * (L + 1) + 2
+    return 5 + 7 + 9 + 1 + 2 * L + 2
+
+
+def gen_hrr(la, lb, lc, ld, cnt):
+    """HRR on the contracted [e0|f0]: returns lines and the name map of final x(a,b,c,d)."""
+    lines = []
+    fl = [f for lf in range(lc, lc + ld + 1) for f in CART[lf]]
+    # bra: (a b| f) from (e 0| f)
+    bra_name = {}
+
+    def bname(a, b, f):
+        return f"hb{tstr(a)}_{tstr(b)}_{tstr(f)}"
+
+    for f in fl:
+        memo = {}
+
+        def need(a, b):
+            if (a, b) in memo:
+                return memo[(a, b)]
+            if b == Z3:
+                nm = f"acc{tstr(a)}_{tstr(f)}"
+                memo[(a, b)] = nm
+                return nm
+            i = first_nz(b)
+            n1 = need(add(a, i), sub(b, i))
+            n2 = need(a, sub(b, i))
+            nm = bname(a, b, f)
+            lines.append(f"const real {nm} = {n1} + AB{AX[i]} * {n2};")
+            cnt.cont += 2
+            memo[(a, b)] = nm
+            return nm
+
+        for a in CART[la]:
+            for b in CART[lb]:
+                bra_name[(a, b, f)] = need(a, b)
+    # ket: (a b| c d) from (a b| f 0)
+    xname = {}
+    for a in CART[la]:
+        for b in CART[lb]:
+            memo = {}
+
+            def need2(c, d):
+                if (c, d) in memo:
+                    return memo[(c, d)]
+                if d == Z3:
+                    nm = bra_name[(a, b, c)]
+                    memo[(c, d)] = nm
+                    return nm
+                i = first_nz(d)
+                n1 = need2(add(c, i), sub(d, i))
+                n2 = need2(c, sub(d, i))
+                nm = f"hk{tstr(a)}_{tstr(b)}_{tstr(c)}_{tstr(d)}"
+                lines.append(f"const real {nm} = {n1} + CD{AX[i]} * {n2};")
+                cnt.cont += 2
+                memo[(c, d)] = nm
+                return nm
+
+            for c in CART[lc]:
+                for d in CART[ld]:
+                    xname[(cidx(a), cidx(b), cidx(c), cidx(d))] = need2(c, d)
+    return lines, xname
+
+
+def gen_digest(la, lb, lc, ld, xname, cnt):
+    na, nb, nc, nd = len(CART[la]), len(CART[lb]), len(CART[lc]), len(CART[ld])
+    lines = []
+
+    def x(a, b, c, d):
+        return xname[(a, b, c, d)]
+
+    def pload(tag, r0, n0, c0, n1):
+        out = []
+        for u in range(n0):
+            for v in range(n1):
+                out.append(f"const real P{tag}_{u}_{v} = (real)Pd[(size_t)({r0} + {u}) * N + {c0} + {v}];")
+        return out
+
+    # density blocks
+    lines += pload("cd", "bC", nc, "bD", nd)
+    lines += pload("ab", "bA", na, "bB", nb)
+    lines += pload("bd", "bB", nb, "bD", nd)
+    lines += pload("ac", "bA", na, "bC", nc)
+    lines += pload("bc", "bB", nb, "bC", nc)
+    lines += pload("ad", "bA", na, "bD", nd)
+
+    def block(target, r0, n0, c0, n1, terms, scale):
+        for u in range(n0):
+            for v in range(n1):
+                ts = terms(u, v)
+                expr = " + ".join(f"{xx} * {pp}" for xx, pp in ts)
+                cnt.cont += 2 * len(ts) + 1
+                lines.append(f"red_add(&{target}[(size_t)({r0} + {u}) * N + {c0} + {v}], (double)({scale} * ({expr})));")
+
+    block("Jt", "bA", na, "bB", nb, lambda a, b: [(x(a, b, c, d), f"Pcd_{c}_{d}") for c in range(nc) for d in range(nd)], "fj")
+    block("Jt", "bC", nc, "bD", nd, lambda c, d: [(x(a, b, c, d), f"Pab_{a}_{b}") for a in range(na) for b in range(nb)], "fj")
+    block("Kt", "bA", na, "bC", nc, lambda a, c: [(x(a, b, c, d), f"Pbd_{b}_{d}") for b in range(nb) for d in range(nd)], "fk")
+    block("Kt", "bB", nb, "bD", nd, lambda b, d: [(x(a, b, c, d), f"Pac_{a}_{c}") for a in range(na) for c in range(nc)], "fk")
+    block("Kt", "bA", na, "bD", nd, lambda a, d: [(x(a, b, c, d), f"Pbc_{b}_{c}") for b in range(nb) for c in range(nc)], "fk")
+    block("Kt", "bB", nb, "bC", nc, lambda b, c: [(x(a, b, c, d), f"Pad_{a}_{d}") for a in range(na) for d in range(nd)], "fk")
+    return lines
+
+
+def gen_schwarz(la, lb, xname):
+    """max over (a,b) of |(ab|ab)| times the component-normalisation factors."""
+    na, nb = len(CART[la]), len(CART[lb])
+    lines = ["double qmax = 0.0;"]
+    for a in range(na):
+        for b in range(nb):
+            na_ = comp_norm2(CART[la][a]) * comp_norm2(CART[lb][b])
+            lines.append(f"qmax = fmax(qmax, fabs((double){xname[(a, b, a, b)]}) * {na_!r});")
+    return lines
+
+
+def comp_norm2(t):
+    """Square of the Cartesian component factor 1/sqrt((2i-1)!!(2j-1)!!(2k-1)!!)."""
+    def df(n):
+        r = 1
+        while n > 1:
+            r *= n
+            n -= 2
+        return r
+    return 1.0 / (df(2 * t[0] - 1) * df(2 * t[1] - 1) * df(2 * t[2] - 1))
+
+
+def class_name(X, Y):
+    la, lb = PAIR_CLASSES[X]
+    lc, ld = PAIR_CLASSES[Y]
+    return f"{la}{lb}{lc}{ld}"
+
+
+def gen_class(X, Y):
+    la, lb = PAIR_CLASSES[X]
+    lc, ld = PAIR_CLASSES[Y]
+    L = la + lb + lc + ld
+    name = class_name(X, Y)
+    cnt = Counter()
+    vrr, acc, used, targets = gen_vrr(la, lb, lc, ld, cnt)
+    setup, cset = gen_setup(L, used, cnt)
+    hrr, xname = gen_hrr(la, lb, lc, ld, cnt)
+    cont_hrr = cnt.cont
+    dig = gen_digest(la, lb, lc, ld, xname, cnt)
+    prim_flops = cnt.prim + cset + boys_flops(L)
+    acc_decl = [f"real acc{tstr(e)}_{tstr(f)} = real(0);" for (e, f, m) in targets]
+    need_ab = any("AB" in l for l in hrr)
+    need_cd = any("CD" in l for l in hrr)
+
+    out = []
+    out.append(f"// ({PAIR_NAMES[X]}|{PAIR_NAMES[Y]}) class: l = {la}{lb}{lc}{ld}, "
+               f"{len(targets)} [e0|f0] targets, {prim_flops} flops per primitive quartet, "
+               f"{cnt.cont} per contracted quartet.")
+    out.append(f"template <typename real>")
+    out.append(f"__device__ __forceinline__ void quartet_{name}(const PairHdr& hb, const PairHdr& hk,"
+               f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
+    out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout)")
+    out.append("{")
+    for l in acc_decl:
+        out.append("    " + l)
+    out.append("    for (int ib = 0; ib < hb.nprim; ib++) {")
+    out.append("        const PrimPair<real> bp = prims[hb.prim0 + ib];")
+    out.append("        const real bK = bp.K, bo2p = bp.oo2p;")
+    for a in AX:
+        if f"PA{a}" in used:
+            out.append(f"        const real PA{a} = bp.PA{a};")
+    out.append("        for (int ik = 0; ik < hk.nprim; ik++) {")
+    out.append("            const PrimPair<real> kp = prims[hk.prim0 + ik];")
+    for l in setup:
+        out.append("            " + l)
+    for l in vrr:
+        out.append("            " + l)
+    for l in acc:
+        out.append("            " + l)
+    out.append("        }")
+    out.append("    }")
+    if need_ab:
+        out.append("    const real ABx = (real)hb.ABx, ABy = (real)hb.ABy, ABz = (real)hb.ABz;")
+    if need_cd:
+        out.append("    const real CDx = (real)hk.ABx, CDy = (real)hk.ABy, CDz = (real)hk.ABz;")
+    for l in hrr:
+        out.append("    " + l)
+    out.append("    if (qout) {")
+    if X == Y:
+        for l in gen_schwarz(la, lb, xname):
+            out.append("        " + l)
+        out.append("        *qout = qmax;")
+    out.append("        return;")
+    out.append("    }")
+    out.append("    const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
+    out.append("    const real fj = (real)(4.0 * fscale), fk = (real)(2.0 * fscale);")
+    for l in dig:
+        out.append("    " + l)
+    out.append("}")
+    out.append("")
+    out.append(f"ERI_CLASS_KERNELS({name}, {X}, {Y})")
+    if X == Y:
+        out.append(f"SCHWARZ_KERNEL({name})")
+    info = dict(name=name, X=X, Y=Y, l=[la, lb, lc, ld], L=L, prim_flops=prim_flops, cont_flops=cnt.cont,
+                hrr_flops=cont_hrr, targets=len(targets), vrr_nodes=len(vrr))
+    return "\n".join(out) + "\n", info
+
+
+HEADER = """// Generated by gen_eri.py: do not edit.  One shell-quartet class per file.
+#include "eri_common.cuh"
+
+namespace hf {
+"""
+FOOTER = "}  // namespace hf\n"
+
+
+def main(outdir):
+    os.makedirs(outdir, exist_ok=True)
+    infos = []
+    for X, Y in classes():
+        src, info = gen_class(X, Y)
+        infos.append(info)
+        path = os.path.join(outdir, f"eri_{info['name']}.cu")
+        text = HEADER + src + FOOTER
+        if not os.path.exists(path) or open(path).read() != text:
+            with open(path, "w") as fh:
+                fh.write(text)
+    # dispatch table
+    lines = ['// Generated by gen_eri.py: do not edit.', '#include "eri_common.cuh"', "", "namespace hf {"]
+    for info in infos:
+        n = info["name"]
+        lines.append(f"void launch_eri_{n}(const EriArgs&, int, int, int, cudaStream_t);")
+        if info["X"] == info["Y"]:
+            lines.append(f"void launch_schwarz_{n}(const SchwarzArgs&, int, cudaStream_t);")
+    lines.append("")
+    lines.append("const EriClassEntry kEriClasses[kNumClasses] = {")
+    for info in infos:
+        n = info["name"]
+        lines.append(f"    {{{info['X']}, {info['Y']}, {info['L']}, {info['prim_flops']}, {info['cont_flops']}, "
+                     f"launch_eri_{n}, {('launch_schwarz_' + n) if info['X'] == info['Y'] else 'nullptr'}, \"{n}\"}},")
+    lines.append("};")
+    lines.append("}  // namespace hf")
+    text = "\n".join(lines) + "\n"
+    path = os.path.join(outdir, "eri_table.cu")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+    jpath = os.path.join(outdir, "eri_classes.json")
+    with open(jpath, "w") as fh:
+        json.dump(infos, fh, indent=1)
+    return infos
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else os.path.join(os.path.dirname(os.path.abspath(__file__)), "generated"))

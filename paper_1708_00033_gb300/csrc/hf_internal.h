@@ -1,0 +1,134 @@
+// Internal declarations of the GB300 direct-SCF Fock-build library.
+// Not part of the C-ABI (that is include/hf.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hf.h"
+
+namespace hf {
+
+constexpr int kMaxL = 2;
+constexpr int kNumPairClasses = 6;  // ss ps pp ds dp dd
+constexpr int kNumClasses = 21;     // (X|Y), X >= Y
+constexpr int kMaxPrim = 8;         // primitives per shell accepted by the library
+
+// One significant shell pair, oriented so that l_A >= l_B.
+struct PairHdr {
+    int A, B;          // shell ids
+    int bfA, bfB;      // first basis function of shells A and B
+    int prim0, nprim;  // primitive-pair records [prim0, prim0 + nprim)
+    double ABx, ABy, ABz;
+    double Q;          // Cauchy-Schwarz bound sqrt(max |(mu nu|mu nu)|)
+};
+
+struct EriArgs {
+    const PairHdr* pairs;
+    const void* prims64;  // PrimPair<double>[]
+    const void* prims32;  // PrimPair<float>[]
+    const int* bra;       // bra pair ids (one class, sorted by Q descending)
+    const int* ket;       // ket pair ids
+    const long long* offsets;  // [n_bra + 1] exclusive prefix of quartets per bra
+    const int* kstart;         // [n_bra] first ket of each bra (nullptr: 0)
+    int n_bra;
+    int same;                  // bra and ket lists are the same list
+    long long n_quartets;
+    int N;
+    const double* P64;  // density in the library's raw component normalisation
+    const float* P32;
+    double* Jt;
+    double* Kt;
+    const double* boys64;
+    const float* boys32;
+};
+
+struct SchwarzArgs {
+    const PairHdr* pairs;
+    const void* prims64;  // PrimPair<double>[]
+    const int* ids;       // pair ids of one diagonal class
+    int n;
+    double* Q;            // [pair id] output bound
+    const double* boys64;
+};
+
+struct EriClassEntry {
+    int X, Y, L;
+    int prim_flops;  // per primitive quartet (setup + Boys + VRR + accumulation)
+    int cont_flops;  // per contracted quartet (HRR + digestion)
+    void (*launch)(const EriArgs&, int use_f32, int grid, int block, cudaStream_t);
+    void (*launch_schwarz)(const SchwarzArgs&, int block, cudaStream_t);
+    const char* name;
+};
+extern const EriClassEntry kEriClasses[kNumClasses];
+
+// ---------------------------------------------------------------- errors --
+struct Status {
+    int code = HF_OK;
+    std::string msg;
+};
+void set_error(int code, const std::string& msg);
+int cuda_status(cudaError_t e, const char* what);
+
+#define HF_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_status(e_, #call);  \
+    } while (0)
+
+// -------------------------------------------------- device buffer helper --
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int alloc(size_t n);
+    void release();
+    template <typename T>
+    T* as() const { return (T*)p; }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+};
+
+}  // namespace hf
+
+// ----------------------------------------------------------- C-ABI types --
+struct hf_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    hf::DevBuf boys64, boys32;  // Boys Taylor tables
+    cudaEvent_t ev[4 * hf::kNumClasses + 4] = {};
+    bool events_ready = false;
+};
+
+struct hf_system {
+    hf_ctx* ctx = nullptr;
+    int n_atoms = 0, n_shells = 0, n_bf = 0, n_electrons = 0;
+    double E_nn = 0.0;
+    hf_thresholds th{};
+    // shells (device)
+    hf::DevBuf sh_l, sh_atom, sh_bf0, sh_nprim, sh_prim0, sh_exp, sh_coef, atom_xyz, atom_Z;
+    hf::DevBuf comp_norm;  // [n_bf] Cartesian component factor
+    // pairs
+    int n_pairs_all = 0, n_prim_pairs = 0;
+    hf::DevBuf pairs, prims64, prims32, pair_class;
+    int class_count[hf::kNumPairClasses] = {};
+    hf::DevBuf class_ids[hf::kNumPairClasses];  // sorted significant pair ids
+    double Qmax = 0.0;
+    // quartet schedule per class
+    struct ClassPlan {
+        hf::DevBuf offsets64, offsets32, kstart32;
+        long long n64 = 0, n32 = 0;
+        long long n_unscreened = 0;
+    } plan[hf::kNumClasses];
+    // matrices (device)
+    hf::DevBuf S, H, P64, P32, Jt, Kt, J, K, F, Ebuf, host_stage;
+    int64_t quartets_total = 0;
+    // scratch
+    hf::DevBuf class_q[hf::kNumPairClasses];  // sorted bounds of class_ids
+    hf::DevBuf Qall, counts, staging_P, staging_out, bad;
+    int maxpp = 0;
+};

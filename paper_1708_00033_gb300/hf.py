@@ -1,0 +1,259 @@
+"""Thin Python binding of the C-ABI in include/hf.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libhf.so``; if it is not
+built, loading fails with an error instead of falling back to anything else.
+PyTorch supplies device memory and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhf.so")
+
+HF_OK = 0
+HF_E_INVALID = -1
+HF_E_UNSUPPORTED = -2
+HF_E_NOMEM = -3
+HF_E_CUDA = -4
+HF_E_TIMEOUT = -5
+HF_E_NOCONV = -6
+HF_PTR_HOST = 0
+HF_PTR_DEVICE = 1
+HF_TIMING = 2
+NUM_CLASSES = 21
+
+CLASS_NAMES = []
+for _X, _xn in enumerate(["ss", "ps", "pp", "ds", "dp", "dd"]):
+    for _Y, _yn in enumerate(["ss", "ps", "pp", "ds", "dp", "dd"][: _X + 1]):
+        CLASS_NAMES.append(f"({_xn}|{_yn})")
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class Geometry_c(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("Z", _i32p), ("xyz", _f64p)]
+
+
+class Basis_c(ctypes.Structure):
+    _fields_ = [("n_shells", ctypes.c_int32), ("atom", _i32p), ("l", _i32p), ("nprim", _i32p),
+                ("exps", _f64p), ("coefs", _f64p)]
+
+
+class Thresholds_c(ctypes.Structure):
+    _fields_ = [("schwarz_tau", ctypes.c_double), ("fp32_cutoff", ctypes.c_double), ("prim_tau", ctypes.c_double)]
+
+
+class Stats_c(ctypes.Structure):
+    _fields_ = [("quartets_unscreened", ctypes.c_int64), ("quartets_fp64", ctypes.c_int64),
+                ("quartets_fp32", ctypes.c_int64),
+                ("class_quartets_fp64", ctypes.c_int64 * NUM_CLASSES),
+                ("class_quartets_fp32", ctypes.c_int64 * NUM_CLASSES),
+                ("flops_fp64", ctypes.c_double), ("flops_fp32", ctypes.c_double),
+                ("ms_class_fp64", ctypes.c_float * NUM_CLASSES), ("ms_class_fp32", ctypes.c_float * NUM_CLASSES),
+                ("ms_eri", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+
+class SystemInfo_c(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("n_shells", ctypes.c_int32), ("n_bf", ctypes.c_int32),
+                ("n_electrons", ctypes.c_int32), ("n_pairs", ctypes.c_int64), ("n_significant_pairs", ctypes.c_int64),
+                ("quartets_unscreened", ctypes.c_int64), ("quartets_fp64", ctypes.c_int64),
+                ("quartets_fp32", ctypes.c_int64), ("E_nn", ctypes.c_double), ("Q_max", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class HFError(RuntimeError):
+    def __init__(self, code, where, msg):
+        super().__init__(f"{where}: status {code} ({msg})")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library():
+    """Load libhf.so; raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_1708_00033_gb300.build() on a machine with nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    lib.hf_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+    lib.hf_destroy.argtypes = [vp]
+    lib.hf_destroy.restype = None
+    lib.hf_strerror.argtypes = [ctypes.c_int]
+    lib.hf_strerror.restype = ctypes.c_char_p
+    lib.hf_last_error.argtypes = []
+    lib.hf_last_error.restype = ctypes.c_char_p
+    lib.hf_system_create.argtypes = [vp, ctypes.POINTER(Geometry_c), ctypes.POINTER(Basis_c),
+                                     ctypes.POINTER(Thresholds_c), ctypes.POINTER(vp)]
+    lib.hf_system_destroy.argtypes = [vp]
+    lib.hf_system_destroy.restype = None
+    lib.hf_system_get_info.argtypes = [vp, ctypes.POINTER(SystemInfo_c)]
+    lib.hf_one_electron.argtypes = [vp, vp, vp, ctypes.c_int]
+    lib.hf_fock_build.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Stats_c),
+                                  ctypes.c_int]
+    _lib = lib
+    return lib
+
+
+def _check(rc, where):
+    if rc != HF_OK:
+        lib = load_library()
+        raise HFError(rc, where, lib.hf_last_error().decode() or lib.hf_strerror(rc).decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """hf_create: one device, one stream (torch's current stream by default)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._h = ctypes.c_void_p()
+        _check(load_library().hf_create(ctypes.byref(self._h), self.device, ctypes.c_void_p(handle)), "hf_create")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().hf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _as_i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _as_f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class System:
+    """hf_system_create: one molecule with its screening plan."""
+
+    def __init__(self, ctx: Context, geom: _inputs.Geometry, basis: _inputs.Basis, schwarz_tau: float = 0.0,
+                 fp32_cutoff: float = 0.0):
+        self.ctx = ctx
+        Z, xyz = _as_i32(geom.Z), _as_f64(geom.xyz)
+        at, l, npr = _as_i32(basis.atom), _as_i32(basis.l), _as_i32(basis.nprim)
+        ex, co = _as_f64(basis.exps), _as_f64(basis.coefs)
+        g = Geometry_c(int(Z.shape[0]), Z.ctypes.data_as(_i32p), xyz.ctypes.data_as(_f64p))
+        b = Basis_c(int(l.shape[0]), at.ctypes.data_as(_i32p), l.ctypes.data_as(_i32p), npr.ctypes.data_as(_i32p),
+                    ex.ctypes.data_as(_f64p), co.ctypes.data_as(_f64p))
+        th = Thresholds_c(float(schwarz_tau), float(fp32_cutoff), 0.0)
+        self._h = ctypes.c_void_p()
+        _check(load_library().hf_system_create(ctx._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(th),
+                                               ctypes.byref(self._h)), "hf_system_create")
+        self.info = self.get_info()
+        self.n_bf = self.info["n_bf"]
+
+    def get_info(self) -> dict:
+        inf = SystemInfo_c()
+        _check(load_library().hf_system_get_info(self._h, ctypes.byref(inf)), "hf_system_get_info")
+        return {k: getattr(inf, k) for k, _ in SystemInfo_c._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().hf_system_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def one_electron(self, device: bool = False):
+        N = self.n_bf
+        if device:
+            torch = _torch()
+            S = torch.empty((N, N), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+            H = torch.empty_like(S)
+            _check(load_library().hf_one_electron(self._h, S.data_ptr(), H.data_ptr(), HF_PTR_DEVICE),
+                   "hf_one_electron")
+            return S, H
+        S, H = np.empty((N, N)), np.empty((N, N))
+        _check(load_library().hf_one_electron(self._h, S.ctypes.data, H.ctypes.data, HF_PTR_HOST), "hf_one_electron")
+        return S, H
+
+    def fock_build(self, P, F=None, J=None, K=None, want_J=False, want_K=False, energy=True, stats=False,
+                   timing=False):
+        """hf_fock_build.  ``P`` may be a numpy array (host path: copies in the
+        timed call) or a CUDA float64 tensor (device path).  Output buffers may
+        be passed to avoid allocation.  Returns a dict with F, J, K, E_elec and
+        optionally stats."""
+        N = self.n_bf
+        lib = load_library()
+        flags = HF_TIMING if timing else 0
+        is_dev = hasattr(P, "is_cuda") and P.is_cuda
+        if is_dev:
+            torch = _torch()
+            if P.dtype != torch.float64 or not P.is_contiguous() or tuple(P.shape) != (N, N):
+                raise ValueError("P must be a contiguous float64 N x N CUDA tensor")
+            flags |= HF_PTR_DEVICE
+            if F is None:
+                F = torch.empty_like(P)
+            if want_J and J is None:
+                J = torch.empty_like(P)
+            if want_K and K is None:
+                K = torch.empty_like(P)
+            ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+            p_ptr = P.data_ptr()
+        else:
+            P = _as_f64(P)
+            if P.shape != (N, N):
+                raise ValueError("P must be N x N")
+            if F is None:
+                F = np.empty((N, N))
+            if want_J and J is None:
+                J = np.empty((N, N))
+            if want_K and K is None:
+                K = np.empty((N, N))
+            ptr = lambda a: a.ctypes.data if a is not None else None  # noqa: E731
+            p_ptr = P.ctypes.data
+        e = ctypes.c_double(0.0)
+        st = Stats_c()
+        rc = lib.hf_fock_build(self._h, p_ptr, ptr(F), ptr(J), ptr(K), ctypes.byref(e) if energy else None,
+                               ctypes.byref(st) if (stats or timing) else None, flags)
+        _check(rc, "hf_fock_build")
+        out = {"F": F, "J": J, "K": K, "E_elec": e.value if energy else None}
+        if stats or timing:
+            out["stats"] = stats_dict(st)
+        return out
+
+
+def stats_dict(st: Stats_c) -> dict:
+    d = {k: getattr(st, k) for k, _ in Stats_c._fields_}
+    for k in ("class_quartets_fp64", "class_quartets_fp32", "ms_class_fp64", "ms_class_fp32"):
+        d[k] = list(d[k])
+    return d
+
+
+def exported_symbols() -> list[str]:
+    """Names declared in include/hf.h (functions only)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "hf.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"\b(hf_[a-z_0-9]+)\s*\(", txt)))
