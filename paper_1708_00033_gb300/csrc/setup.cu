@@ -132,7 +132,7 @@ __global__ void k_build_pairs(long long n_pairs, int maxpp, const int* __restric
     h.Q = 0.0;
     pairs[t] = h;
     pclass[t] = la * (la + 1) / 2 + lb;
-    const double c52 = 1.4142135623730950488 * 4.1327313541224929385;  // sqrt(2) pi^(5/4)
+    const double c52 = sqrt(2.0) * pow(M_PI, 1.25);  // sqrt(2) pi^(5/4)
     int k = 0;
     for (int ka = 0; ka < nprim[A]; ka++) {
         const double a = exps[prim0[A] + ka], ca = cn[prim0[A] + ka];
