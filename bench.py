@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Fock builds/s of the GB300 direct-SCF Fock build (one JSON line on stdout).
+
+Workload (default): the 64-water cluster of the SCF configuration (seed
+(2, rank)), 1,600 Cartesian basis functions, Schwarz screening at 1e-10,
+plain FP64 integrals; one step = one full Fock build (density in, J and K of
+all 21 angular classes, F = H + J - K/2 and the energy out).  With N ranks
+each rank builds its own cluster (independent problems, weak scaling, no
+collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (as it stands) on the host cores over
+strided samples of the same Fock build and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DFMA_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal, derived)
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--waters", type=int, default=64)
+    ap.add_argument("--config-id", type=int, default=2)
+    ap.add_argument("--tau", type=float, default=1e-10)
+    ap.add_argument("--fp32-cutoff", type=float, default=0.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_name(a):
+    prec = "FP64" if a.fp32_cutoff <= 0 else f"mixed FP32<{a.fp32_cutoff:g}"
+    return (f"{a.waters}-water cluster, {25 * a.waters} Cartesian BF, synthetic 3-primitive basis, "
+            f"Schwarz tau={a.tau:g}, {prec} Fock build (J+K)")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def random_density(S, n_occ, cfg, idx):
+    """P = 2 C C^T with C = G L^-T, L L^T = G^T S G (input preparation, untimed)."""
+    import numpy as np
+    from paper_1708_00033_gb300 import inputs
+    G = inputs.random_orbitals(S.shape[0], n_occ, cfg, idx)
+    L = np.linalg.cholesky(G.T @ S @ G)
+    C = np.linalg.solve(L, G.T).T
+    return 2.0 * C @ C.T
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        out["sm_mhz"] = statistics.median(float(r[1]) for r in rows)
+        out["sm_max_mhz"] = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(rows)
+        return out
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1708_00033_gb300 import hf, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    geom = inputs.water_cluster(a.waters, a.config_id, rank)
+    basis = inputs.synthetic_basis(geom)
+    ctx = hf.Context(local)
+    sysm = hf.System(ctx, geom, basis, schwarz_tau=a.tau, fp32_cutoff=a.fp32_cutoff)
+    N = sysm.n_bf
+    S, _ = sysm.one_electron()
+    n_occ = inputs.n_electrons(geom) // 2
+    P = random_density(S, n_occ, a.config_id, rank)
+    Pd = torch.from_numpy(P).to(dev)
+    Fd = torch.empty_like(Pd)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(a.warmup):
+        sysm.fock_build(Pd, F=Fd)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, stats = [], []
+    torch.cuda.synchronize()
+    for _ in range(a.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = sysm.fock_build(Pd, F=Fd, timing=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(out["stats"])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = world * a.steps / (total_ms / 1e3)
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timing
+    e2e = None
+    if not a.no_e2e:
+        Ph = torch.from_numpy(P).pin_memory()
+        Fh = torch.empty((N, N), dtype=torch.float64).pin_memory()
+        sysm.fock_build(Ph.numpy(), F=Fh.numpy())
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            sysm.fock_build(Ph.numpy(), F=Fh.numpy())
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * a.steps / dt, "unit": "Fock builds/s", "h2d_bytes_per_step": N * N * 8,
+               "d2h_bytes_per_step": N * N * 8 + 8}
+
+    # roofline of the dominant kernel (the class kernel with the largest device time)
+    ms_cls = np.mean([s["ms_class_fp64"] for s in stats], axis=0) + np.mean([s["ms_class_fp32"] for s in stats], axis=0)
+    c = int(np.argmax(ms_cls))
+    fl = stats[0]["class_flops_fp64"][c] + stats[0]["class_flops_fp32"][c]
+    achieved = fl / (ms_cls[c] / 1e3) / 1e9
+    eri_ms = float(np.mean([s["ms_eri"] for s in stats]))
+    eri_gflops = stats[0]["flops_fp64"] / (eri_ms / 1e3) / 1e9
+    line = {
+        "metric": "Fock builds/s",
+        "value": value,
+        "unit": "Fock builds/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if a.fp32_cutoff <= 0 else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(a), "waters": a.waters, "n_bf": N, "schwarz_tau": a.tau,
+                   "fp32_cutoff": a.fp32_cutoff, "density": "random S-orthonormal C, n_occ=%d" % n_occ,
+                   "quartets_evaluated": stats[0]["quartets_fp64"] + stats[0]["quartets_fp32"],
+                   "quartets_unscreened": stats[0]["quartets_unscreened"],
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "gpu_launches": int(sum(s["kernels_launched"] for s in stats)),
+        "clocks": clk,
+        "roofline": {"bound": "alu", "kernel": hf.CLASS_KERNELS[c], "class": hf.CLASS_NAMES[c], "achieved": achieved,
+                     "peak": DFMA_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / DFMA_PEAK_GFLOPS,
+                     "traffic": None, "peak_kind": "FP64 FMA pipe, derived from unit counts and max clock",
+                     "all_eri_kernels": {"ms": eri_ms, "achieved": eri_gflops,
+                                         "frac": eri_gflops / DFMA_PEAK_GFLOPS}},
+        "class_ms": {hf.CLASS_NAMES[i]: round(float(ms_cls[i]), 3) for i in range(len(ms_cls))},
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, geom, basis, P, a.cpu_sample_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(a, geom, basis, P, seconds, offset=0, mol=None):
+    """Time the oracle on every stride-th bra pair; extrapolate to one build."""
+    import oracle
+    if mol is None:
+        mol = oracle.Molecule(geom, basis)
+    mol.schwarz()  # setup, untimed
+    n_sh = mol.n_shells
+    n_p = n_sh * (n_sh + 1) // 2
+    total_unscreened = n_p * (n_p + 1) // 2
+    # calibrate the stride on a tiny sample
+    stride = max(1, n_p // 8)
+    t0 = time.perf_counter()
+    _, u0 = mol.jk_unique_sample(P, a.tau, stride, offset)
+    dt0 = max(time.perf_counter() - t0, 1e-3)
+    rate = u0 / dt0
+    stride = max(1, int(stride * (dt0 / seconds)) if dt0 < seconds else stride)
+    t0 = time.perf_counter()
+    nq, u = mol.jk_unique_sample(P, a.tau, stride, offset)
+    dt = time.perf_counter() - t0
+    build_s = dt * total_unscreened / max(u, 1)
+    return mol, {"seconds": dt, "stride": stride, "quartets": nq, "unscreened_rows": u,
+                 "est_build_s": build_s, "value": 1.0 / build_s, "rate_hint": rate}
+
+
+def cpu_baseline(a, geom, basis, P, seconds):
+    import oracle
+    _, r = _oracle_sample(a, geom, basis, P, seconds)
+    return {"value": r["value"], "unit": "Fock builds/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"oracle unique-quartet digestion over every {r['stride']}-th bra shell pair "
+                       f"({r['quartets']} screened quartets, {r['seconds']:.1f} s), scaled by the unscreened "
+                       f"quartets the sampled rows span to one full build ({r['est_build_s']:.0f} s)")}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1708_00033_gb300 import inputs
+    geom = inputs.water_cluster(a.waters, a.config_id, 0)
+    basis = inputs.synthetic_basis(geom)
+    mol = oracle.Molecule(geom, basis)
+    S, _ = mol.core_hamiltonian()
+    P = random_density(S, inputs.n_electrons(geom) // 2, a.config_id, 0)
+    per_step = max(2.0, 150.0 / max(1, a.steps + a.warmup))
+    for w in range(a.warmup):
+        _oracle_sample(a, geom, basis, P, per_step / 4, offset=w, mol=mol)
+    est = []
+    for k in range(a.steps):
+        _, r = _oracle_sample(a, geom, basis, P, per_step, offset=a.warmup + k, mol=mol)
+        est.append(r)
+    build_s = sum(r["est_build_s"] for r in est) / len(est)
+    value = 1.0 / build_s
+    line = {"metric": "Fock builds/s", "value": value, "unit": "Fock builds/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": build_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_name(a), "waters": a.waters, "schwarz_tau": a.tau},
+            "cpu_baseline": {"value": value, "unit": "Fock builds/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{a.steps} strided bra-pair samples of ~{per_step:.0f} s each, scaled to one build"},
+            "e2e": {"value": value, "unit": "Fock builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

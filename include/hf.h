@@ -106,6 +106,9 @@ typedef struct {
     float ms_class_fp32[HF_NUM_CLASSES];
     float ms_eri;   /* device time of all ERI kernels (HF_TIMING) */
     float ms_total; /* device time of the whole build (HF_TIMING) */
+    double class_flops_fp64[HF_NUM_CLASSES]; /* algorithmic operations per class kernel */
+    double class_flops_fp32[HF_NUM_CLASSES];
+    int32_t kernels_launched; /* library kernels launched by this call */
 } hf_stats;
 
 /* Sizes of a system. */

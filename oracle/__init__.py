@@ -72,6 +72,8 @@ def _load():
     lib.or_jk_literal.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp]
     lib.or_jk_unique.restype = ctypes.c_int64
     lib.or_jk_unique.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, _dp, _dp]
+    lib.or_jk_unique_sample.restype = ctypes.c_int64
+    lib.or_jk_unique_sample.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, ctypes.c_int64, ctypes.c_int64, _dp, _dp, ctypes.POINTER(ctypes.c_int64)]
     lib.or_jk_elements.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, ctypes.c_int, _ip, _ip, _dp, _dp]
     lib.or_num_threads.restype = ctypes.c_int
     _lib = lib
@@ -210,6 +212,18 @@ class Molecule:
         n = _load().or_jk_unique(self._h, _d(P), float(tau), _d(np.ascontiguousarray(Q)), _d(J), _d(K))
         self.last_quartets = int(n)
         return J, K
+
+    def jk_unique_sample(self, P: np.ndarray, tau: float, stride: int, offset: int = 0):
+        """Unique-quartet digestion over every stride-th bra pair; returns
+        (quartets evaluated, unscreened quartets the sampled rows span)."""
+        N = self.n_bf
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        J, K = np.zeros((N, N)), np.zeros((N, N))
+        Q = self.schwarz() if tau > 0 else np.zeros((1, 1))
+        u = ctypes.c_int64(0)
+        n = _load().or_jk_unique_sample(self._h, _d(P), float(tau), _d(np.ascontiguousarray(Q)), int(stride),
+                                        int(offset), _d(J), _d(K), ctypes.byref(u))
+        return int(n), int(u.value)
 
     def jk_elements(self, P: np.ndarray, pairs, tau: float = 0.0):
         P = np.ascontiguousarray(P, dtype=np.float64)

@@ -553,7 +553,32 @@ void or_jk_literal(int N, const double* eri, const double* P, double* J, double*
  * Thread-private accumulators, summed at the end (the private-Fock pattern
  * of Algorithm 2).  Returns the number of shell quartets evaluated.
  */
+static int64_t jk_unique_impl(void* h, const double* P, double tau, const double* Qsh, int64_t stride,
+                              int64_t offset, double* J, double* K);
+
 int64_t or_jk_unique(void* h, const double* P, double tau, const double* Qsh, double* J, double* K)
+{
+    return jk_unique_impl(h, P, tau, Qsh, 1, 0, J, K);
+}
+
+/*
+ * The same digestion restricted to the bra pairs ij = offset, offset+stride,
+ * ... (a representative sample of Algorithm 1's outer loop, used to time the
+ * oracle on large systems).  *unscreened receives the number of (ij, kl)
+ * combinations the sampled rows span before screening.
+ */
+int64_t or_jk_unique_sample(void* h, const double* P, double tau, const double* Qsh, int64_t stride, int64_t offset,
+                            double* J, double* K, int64_t* unscreened)
+{
+    or_ctx* c = (or_ctx*)h;
+    int64_t np = (int64_t)c->n_shells * (c->n_shells + 1) / 2, u = 0;
+    for (int64_t ij = offset; ij < np; ij += stride) u += ij + 1;
+    *unscreened = u;
+    return jk_unique_impl(h, P, tau, Qsh, stride, offset, J, K);
+}
+
+static int64_t jk_unique_impl(void* h, const double* P, double tau, const double* Qsh, int64_t stride,
+                              int64_t offset, double* J, double* K)
 {
     or_ctx* c = (or_ctx*)h;
     int n = c->n_shells, N = c->n_bf;
@@ -566,7 +591,7 @@ int64_t or_jk_unique(void* h, const double* P, double tau, const double* Qsh, do
         double* Kp = (double*)calloc((size_t)N * N, sizeof(double));
         double blk[OR_MAXCOMP * OR_MAXCOMP * OR_MAXCOMP * OR_MAXCOMP];
 #pragma omp for schedule(dynamic, 1)
-        for (int64_t ij = 0; ij < (int64_t)n * (n + 1) / 2; ij++) {
+        for (int64_t ij = offset; ij < (int64_t)n * (n + 1) / 2; ij += stride) {
             int i = (int)((sqrt(8.0 * ij + 1.0) - 1.0) / 2.0);
             while ((int64_t)i * (i + 1) / 2 > ij) i--;
             while ((int64_t)(i + 1) * (i + 2) / 2 <= ij) i++;

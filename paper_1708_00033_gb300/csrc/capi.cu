@@ -553,13 +553,17 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
             stats->quartets_fp64 += pl.n64;
             stats->quartets_fp32 += pl.n32;
             const double per = kEriClasses[ci].prim_flops * pq + kEriClasses[ci].cont_flops;
+            stats->class_flops_fp64[ci] = per * (double)pl.n64;
+            stats->class_flops_fp32[ci] = per * (double)pl.n32;
             stats->flops_fp64 += per * (double)pl.n64;
             stats->flops_fp32 += per * (double)pl.n32;
+            stats->kernels_launched += (pl.n64 > 0) + (pl.n32 > 0);
             if (timing) {
                 cudaEventElapsedTime(&stats->ms_class_fp64[ci], ctx->ev[4 * ci], ctx->ev[4 * ci + 1]);
                 cudaEventElapsedTime(&stats->ms_class_fp32[ci], ctx->ev[4 * ci + 2], ctx->ev[4 * ci + 3]);
             }
         }
+        stats->kernels_launched += 2 + (E_elec ? 2 : 0);  // density scaling, assembly, energy
         if (timing) {
             cudaEventElapsedTime(&stats->ms_eri, ctx->ev[4 * kNumClasses + 1], ctx->ev[4 * kNumClasses + 2]);
             cudaEventElapsedTime(&stats->ms_total, ctx->ev[4 * kNumClasses], ctx->ev[4 * kNumClasses + 3]);

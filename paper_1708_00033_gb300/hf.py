@@ -33,6 +33,10 @@ for _X, _xn in enumerate(["ss", "ps", "pp", "ds", "dp", "dd"]):
     for _Y, _yn in enumerate(["ss", "ps", "pp", "ds", "dp", "dd"][: _X + 1]):
         CLASS_NAMES.append(f"({_xn}|{_yn})")
 
+PAIR_L = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+CLASS_KERNELS = [f"k_eri_{PAIR_L[X][0]}{PAIR_L[X][1]}{PAIR_L[Y][0]}{PAIR_L[Y][1]}"
+                 for X in range(6) for Y in range(X + 1)]
+
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)
 
@@ -57,7 +61,9 @@ class Stats_c(ctypes.Structure):
                 ("class_quartets_fp32", ctypes.c_int64 * NUM_CLASSES),
                 ("flops_fp64", ctypes.c_double), ("flops_fp32", ctypes.c_double),
                 ("ms_class_fp64", ctypes.c_float * NUM_CLASSES), ("ms_class_fp32", ctypes.c_float * NUM_CLASSES),
-                ("ms_eri", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_eri", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("class_flops_fp64", ctypes.c_double * NUM_CLASSES), ("class_flops_fp32", ctypes.c_double * NUM_CLASSES),
+                ("kernels_launched", ctypes.c_int32)]
 
 
 class SystemInfo_c(ctypes.Structure):
@@ -246,7 +252,8 @@ class System:
 
 def stats_dict(st: Stats_c) -> dict:
     d = {k: getattr(st, k) for k, _ in Stats_c._fields_}
-    for k in ("class_quartets_fp64", "class_quartets_fp32", "ms_class_fp64", "ms_class_fp32"):
+    for k in ("class_quartets_fp64", "class_quartets_fp32", "ms_class_fp64", "ms_class_fp32", "class_flops_fp64",
+              "class_flops_fp32"):
         d[k] = list(d[k])
     return d
 
