@@ -132,8 +132,9 @@ typedef struct {
  * HF_E_UNSUPPORTED (device is not compute capability 10.3), HF_E_CUDA. */
 int hf_create(hf_ctx** ctx, int device, void* cuda_stream);
 
-/* Release a context (NULL is ignored).  Systems created on it must be
- * destroyed first. */
+/* Release a context (NULL is ignored).  If systems created on it are still
+ * alive, the context stays usable by them and is released together with the
+ * last of them. */
 void hf_destroy(hf_ctx* ctx);
 
 /* Short text for a status code; never NULL. */

@@ -173,14 +173,23 @@ int hf_create(hf_ctx** out, int device, void* cuda_stream)
     return HF_OK;
 }
 
-void hf_destroy(hf_ctx* c)
+static void ctx_release(hf_ctx* c)
 {
-    if (!c) return;
     DeviceGuard g(c->device);
     if (c->events_ready)
         for (auto& ev : c->ev)
             if (ev) cudaEventDestroy(ev);
     delete c;
+}
+
+void hf_destroy(hf_ctx* c)
+{
+    if (!c) return;
+    if (c->n_systems > 0) {  // released together with its last system
+        c->destroy_pending = true;
+        return;
+    }
+    ctx_release(c);
 }
 
 }  // extern "C"
@@ -399,6 +408,8 @@ int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis
     DeviceGuard g(ctx->device);
     hf_system* S = new hf_system();
     S->ctx = ctx;
+    S->device = ctx->device;
+    S->stream = ctx->stream;
     if (th) S->th = *th;
     int rc = system_setup(S, geom, basis);
     if (rc != HF_OK) {
@@ -406,6 +417,7 @@ int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis
         delete S;
         return rc;
     }
+    ctx->n_systems++;
     *out = S;
     return HF_OK;
 }
@@ -413,9 +425,13 @@ int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis
 void hf_system_destroy(hf_system* S)
 {
     if (!S) return;
-    DeviceGuard g(S->ctx->device);
-    cudaStreamSynchronize(S->ctx->stream);
-    delete S;
+    hf_ctx* ctx = S->ctx;
+    {
+        DeviceGuard g(S->device);
+        cudaStreamSynchronize(S->stream);
+        delete S;
+    }
+    if (ctx && --ctx->n_systems == 0 && ctx->destroy_pending) ctx_release(ctx);
 }
 
 int hf_system_get_info(const hf_system* S, hf_system_info* info)

@@ -102,10 +102,14 @@ struct hf_ctx {
     hf::DevBuf boys64, boys32;  // Boys Taylor tables
     cudaEvent_t ev[4 * hf::kNumClasses + 4] = {};
     bool events_ready = false;
+    int n_systems = 0;            // live systems created on this context
+    bool destroy_pending = false;  // hf_destroy was called while systems were alive
 };
 
 struct hf_system {
     hf_ctx* ctx = nullptr;
+    int device = 0;               // copies of the context's device and stream, so that
+    cudaStream_t stream = nullptr;  // destruction never needs the context
     int n_atoms = 0, n_shells = 0, n_bf = 0, n_electrons = 0;
     double E_nn = 0.0;
     hf_thresholds th{};

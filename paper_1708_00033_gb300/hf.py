@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 import numpy as np
 
@@ -142,6 +143,8 @@ class Context:
             self._h = None
 
     def __del__(self):
+        if sys.is_finalizing():  # the CUDA runtime may already be gone
+            return
         try:
             self.close()
         except Exception:
@@ -186,6 +189,8 @@ class System:
             self._h = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
