@@ -180,6 +180,31 @@ int hf_one_electron(hf_system* sys, double* S, double* H, int flags);
 int hf_fock_build(hf_system* sys, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
                   int flags);
 
+/* ------------------------------------------------- allocation-free build */
+
+/* Largest system (basis functions) hf_fock_build_noalloc accepts. */
+#define HF_NOALLOC_MAX_BF 512
+
+/* The Fock build of hf_fock_build for callers that cannot allocate device
+ * memory during the call (a process whose device memory is reserved or owned
+ * by a pool that forbids cudaMalloc, or code that must not enter the
+ * allocator at this point).  The paper has no counterpart: it is a property of
+ * this library's interface, not of the method.
+ *   P       [N*N] device pointer, total density (symmetric, finite).
+ *   F       [N*N] device pointer, output H + J - K/2 (required).
+ *   J, K    [N*N] device pointers, outputs (may be NULL).
+ * All pointers are device pointers on the context's device; there is no host
+ * path and no energy or statistics output.  The call allocates nothing: its
+ * scratch (density copy, J/K accumulators, status flag; about 7.3 MB) is one
+ * fixed __device__ array per device, held until the process exits and shared
+ * by every call on that device.  The accumulators are cleared at the start of
+ * each call; calls whose device work overlaps race on the array.  The first
+ * call on a device looks the array's address up once; make it before any
+ * stream capture.  Errors: HF_E_INVALID (NULL sys/P/F, more than
+ * HF_NOALLOC_MAX_BF basis functions, P not finite or not symmetric),
+ * HF_E_CUDA. */
+int hf_fock_build_noalloc(hf_system* sys, const double* P, double* F, double* J, double* K);
+
 #ifdef __cplusplus
 }
 #endif

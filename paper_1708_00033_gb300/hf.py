@@ -109,6 +109,7 @@ def load_library():
     lib.hf_one_electron.argtypes = [vp, vp, vp, ctypes.c_int]
     lib.hf_fock_build.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Stats_c),
                                   ctypes.c_int]
+    lib.hf_fock_build_noalloc.argtypes = [vp, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -253,6 +254,13 @@ class System:
         if stats or timing:
             out["stats"] = stats_dict(st)
         return out
+
+
+def fock_build_noalloc(system: "System", P, F, J=None, K=None):
+    """hf_fock_build_noalloc: device tensors in and out, no allocation in the call."""
+    ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+    _check(load_library().hf_fock_build_noalloc(system._h, ptr(P), ptr(F), ptr(J), ptr(K)), "hf_fock_build_noalloc")
+    return F
 
 
 def stats_dict(st: Stats_c) -> dict:
