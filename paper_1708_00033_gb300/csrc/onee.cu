@@ -43,7 +43,12 @@ __device__ __forceinline__ double binom(int n, int k)
 
 }  // namespace
 
-// one thread per ordered shell pair (i, j); writes the (i, j) block of S and H
+// one thread per unordered shell pair (i >= j); writes the (i, j) block of S
+// and H and its transpose.  Primitive pairs whose Gaussian-product factor
+// exp(-ab/(a+b) |AB|^2) is below exp(-60) ~ 9e-27 are skipped: with
+// normalised coefficients below 1e3, 2 pi / p below 30, a total nuclear
+// charge below 1e5 and polynomial factors below 1e6 their contribution to
+// any element stays below 1e-12 of the 1e-11 parity tolerance.
 __global__ void k_one_electron(int n_sh, int n_atoms, int N, const int* __restrict__ l, const int* __restrict__ atom,
                                const int* __restrict__ bf0, const int* __restrict__ nprim,
                                const int* __restrict__ prim0, const double* __restrict__ exps,
@@ -52,8 +57,11 @@ __global__ void k_one_electron(int n_sh, int n_atoms, int N, const int* __restri
                                const double* __restrict__ boys64, double* __restrict__ S, double* __restrict__ H)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)n_sh * n_sh) return;
-    const int i = (int)(t / n_sh), j = (int)(t % n_sh);
+    if (t >= (long long)n_sh * (n_sh + 1) / 2) return;
+    long long ii = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (ii * (ii + 1) / 2 > t) ii--;
+    while ((ii + 1) * (ii + 2) / 2 <= t) ii++;
+    const int i = (int)ii, j = (int)(t - ii * (ii + 1) / 2);
     const int la = l[i], lb = l[j];
     const int na = ncomp(la), nb = ncomp(lb);
     const double A[3] = {xyz[3 * atom[i]], xyz[3 * atom[i] + 1], xyz[3 * atom[i] + 2]};
@@ -66,6 +74,9 @@ __global__ void k_one_electron(int n_sh, int n_atoms, int N, const int* __restri
             const double a = exps[prim0[i] + ka], b = exps[prim0[j] + kb];
             const double cc = cn[prim0[i] + ka] * cn[prim0[j] + kb];
             const double p = a + b, mu = a * b / p, o2p = 0.5 / p;
+            const double R2ab = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) +
+                                (A[2] - B[2]) * (A[2] - B[2]);
+            if (mu * R2ab > 60.0) continue;
             double P[3], PA[3], PB[3];
             double s[3][4][4];  // s[dir][i][j], i <= la+1, j <= lb+1
             for (int d = 0; d < 3; d++) {
@@ -161,8 +172,8 @@ __global__ void k_one_electron(int n_sh, int n_atoms, int N, const int* __restri
         for (int cb = 0; cb < nb; cb++) {
             const int r = bf0[i] + ca, c = bf0[j] + cb;
             const double nrm = comp_norm[r] * comp_norm[c];
-            if (S) S[(size_t)r * N + c] = nrm * sblk[ca * nb + cb];
-            if (H) H[(size_t)r * N + c] = nrm * hblk[ca * nb + cb];
+            if (S) S[(size_t)r * N + c] = S[(size_t)c * N + r] = nrm * sblk[ca * nb + cb];
+            if (H) H[(size_t)r * N + c] = H[(size_t)c * N + r] = nrm * hblk[ca * nb + cb];
         }
 }
 
@@ -192,7 +203,7 @@ int launch_one_electron(int n_sh, int n_atoms, int N, const int* l, const int* a
                         const double* xyz, const double* Z, const double* comp_norm, const double* boys64,
                         double* S, double* H, cudaStream_t s)
 {
-    const long long n = (long long)n_sh * n_sh;
+    const long long n = (long long)n_sh * (n_sh + 1) / 2;
     if (n > 0)
         k_one_electron<<<(unsigned)((n + 63) / 64), 64, 0, s>>>(n_sh, n_atoms, N, l, atom, bf0, nprim, prim0, exps, cn,
                                                               xyz, Z, comp_norm, boys64, S, H);
