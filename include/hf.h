@@ -82,7 +82,11 @@ typedef struct {
  *   fp32_cutoff : evaluate a quartet's integrals in FP32 when
  *                 Q_ij * Q_kl < fp32_cutoff (accumulation stays FP64);
  *                 0 keeps every quartet in FP64.
- *   prim_tau    : reserved, must be 0. */
+ *   prim_tau    : skip a primitive quartet when B_ab * B_cd < prim_tau, with
+ *                 B = sqrt(max |[ab|ab]|) the Schwarz bound of one primitive
+ *                 pair (normalised components); 0 evaluates every primitive
+ *                 quartet.  Each skipped primitive quartet changes any
+ *                 integral by at most prim_tau. */
 typedef struct {
     double schwarz_tau;
     double fp32_cutoff;
@@ -109,6 +113,8 @@ typedef struct {
     double class_flops_fp64[HF_NUM_CLASSES]; /* algorithmic operations per class kernel */
     double class_flops_fp32[HF_NUM_CLASSES];
     int32_t kernels_launched; /* library kernels launched by this call */
+    int64_t prim_quartets_fp64; /* primitive quartets evaluated (after primitive screening) */
+    int64_t prim_quartets_fp32;
 } hf_stats;
 
 /* Sizes of a system. */
@@ -151,8 +157,8 @@ const char* hf_last_error(void);
  * by angular class and bound, and the per-class quartet schedule for the
  * given thresholds.  Geometry and basis are read from host memory and not
  * kept.  Errors: HF_E_INVALID (null/negative sizes, atom index out of
- * range, non-positive exponent, NaN), HF_E_UNSUPPORTED (l > 2,
- * nprim > 8, prim_tau != 0), HF_E_NOMEM, HF_E_CUDA. */
+ * range, non-positive exponent, NaN, negative threshold), HF_E_UNSUPPORTED
+ * (l > 2, nprim > 8), HF_E_NOMEM, HF_E_CUDA. */
 int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis, const hf_thresholds* th,
                      hf_system** sys);
 
@@ -179,6 +185,112 @@ int hf_one_electron(hf_system* sys, double* S, double* H, int flags);
  * HF_E_NOMEM, HF_E_CUDA. */
 int hf_fock_build(hf_system* sys, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
                   int flags);
+
+/* ------------------------------------------------------------------- SCF */
+
+/* Options of hf_scf_run (zero-initialise, then set what differs):
+ *   n_occ      doubly occupied orbitals (0: n_electrons / 2)
+ *   max_iter   Fock builds at most (0: 100)
+ *   e_tol      |E_k - E_{k-1}| threshold in Eh (0: 1e-9)
+ *   d_tol      RMS(P_k - P_{k-1}) threshold (0: 1e-6)
+ *   diis_size  Pulay DIIS history length, 0..16 (0 with diis_off = 1 disables)
+ *   diis_off   1 disables DIIS */
+typedef struct {
+    int32_t n_occ;
+    int32_t max_iter;
+    double e_tol;
+    double d_tol;
+    int32_t diis_size;
+    int32_t diis_off;
+} hf_scf_opts;
+
+/* Result of hf_scf_run. */
+typedef struct {
+    double energy;          /* total energy E_elec + E_nn at the last density (Eh) */
+    double E_nn;            /* nuclear repulsion */
+    int32_t iterations;     /* Fock builds performed */
+    int32_t converged;      /* 1 if both thresholds were met */
+    double last_dE, last_dP;
+    double seconds_total;   /* host wall time of the call */
+    double seconds_fock;    /* of which Fock builds */
+    double seconds_diag;    /* of which orthogonalisation + diagonalisation + density */
+    int32_t jacobi_sweeps;  /* total Jacobi sweeps of all diagonalisations */
+    int32_t n_kept;         /* orthogonal basis size (N unless near-linear dependence) */
+    double s_min;           /* smallest overlap eigenvalue */
+} hf_scf_result;
+
+/* Closed-shell SCF (Section 3, Eq. FC = eSC): X = S^-1/2 (canonical
+ * orthogonalisation when an overlap eigenvalue is below 1e-8), guess = core
+ * Hamiltonian unless P_guess is given, then F(P) by hf_fock_build, Pulay DIIS
+ * on FPS - SPF, eigenpairs of X^T F X by the device Jacobi solver,
+ * P = 2 C_occ C_occ^T, until |dE| < e_tol and RMS dP < d_tol.
+ *   P_guess   [N*N] initial density or NULL
+ *   P_out     [N*N] final density (the one F was built from) or NULL
+ *   eps_out   [n_kept] orbital energies of the last diagonalisation or NULL
+ *   energies  host array of max_iter energies per iteration, or NULL
+ *   res       host output (required)
+ * flags: HF_PTR_DEVICE for P_guess / P_out / eps_out.  Errors: HF_E_INVALID,
+ * HF_E_NOMEM, HF_E_CUDA, HF_E_NOCONV (res and P_out then hold the last
+ * iterate). */
+int hf_scf_run(hf_system* sys, const hf_scf_opts* opts, const double* P_guess, double* P_out, double* eps_out,
+               double* energies, hf_scf_result* res, int flags);
+
+/* Eigen-decomposition of a symmetric n x n matrix A on the device (parallel
+ * cyclic Jacobi, the diagonalisation step of Section 3's SCF).  w[n]
+ * eigenvalues ascending; V[n*n] row-major with eigenvector j in column j.
+ * flags: HF_PTR_DEVICE for device pointers.  Errors: HF_E_INVALID,
+ * HF_E_NOMEM, HF_E_CUDA, HF_E_NOCONV (60 sweeps). */
+int hf_eigh(hf_ctx* ctx, int n, const double* A, double* w, double* V, int flags);
+
+/* --------------------------------------------------------------- batches */
+
+typedef struct hf_batch hf_batch; /* many independent molecules built together */
+
+#define HF_BATCH_SEQUENTIAL 4 /* hf_fock_build_batch: one hf_fock_build per molecule instead of the graph */
+
+/* Sizes and tuning of a batch. */
+typedef struct {
+    int32_t n_mol;
+    int64_t packed_len; /* sum of N_m^2: length of the packed matrix arrays */
+    int64_t n_bf_total;
+    int64_t quartets; /* screened shell quartets of one batched build */
+    int64_t class_quartets[HF_NUM_CLASSES];
+    int32_t block[HF_NUM_CLASSES];         /* threads per block of each class kernel */
+    int32_t chunk[HF_NUM_CLASSES];         /* quartets per work-queue grab */
+    int32_t blocks_per_sm[HF_NUM_CLASSES]; /* persistent grid = SMs x blocks_per_sm */
+} hf_batch_info;
+
+/* Set up n_mol independent molecules (geoms[m], bases[m]; thresholds shared,
+ * FP64 integrals: fp32_cutoff is ignored) for batched Fock builds.  The
+ * per-iteration work of the whole batch (density scaling, one persistent
+ * kernel per angular class over every molecule's quartets fed by a device
+ * work queue - the GPU counterpart of Algorithm 1's ddi_dlbnext dynamic load
+ * balancing - assembly and energies) is captured once in a CUDA graph.
+ * Errors as hf_system_create. */
+int hf_batch_create(hf_ctx* ctx, int n_mol, const hf_geometry* geoms, const hf_basis* bases,
+                    const hf_thresholds* th, hf_batch** batch);
+void hf_batch_destroy(hf_batch* batch);
+int hf_batch_get_info(const hf_batch* batch, hf_batch_info* info);
+
+/* off[n_mol + 1]: offset of molecule m's N_m x N_m block in the packed arrays. */
+int hf_batch_offsets(const hf_batch* batch, int64_t* off);
+
+/* One Fock build of every molecule.  P and F are packed arrays (molecule m's
+ * row-major N_m x N_m block at off[m]); host pointers unless HF_PTR_DEVICE.
+ * E_elec: host array of n_mol electronic energies or NULL; ms: host output of
+ * the device time of the build or NULL.  HF_BATCH_SEQUENTIAL runs one
+ * hf_fock_build per molecule instead (the unbatched reference).  Errors:
+ * HF_E_INVALID (NULL argument, a density not finite or not symmetric),
+ * HF_E_CUDA. */
+int hf_fock_build_batch(hf_batch* batch, const double* P, double* F, double* E_elec, float* ms, int flags);
+
+/* Autotuner: for every class kernel, time each candidate (block size 64/128/
+ * 256, chunk 32/128/512 quartets, 2/4/8 blocks per SM) on the first
+ * sample_quartets quartets (0: 2e6) and keep the fastest; choices are read
+ * from and written to cache_path (one "class block chunk blocks_per_sm" line
+ * per class) when it is not NULL.  Re-captures the graph.  Errors: HF_E_INVALID,
+ * HF_E_CUDA. */
+int hf_batch_tune(hf_batch* batch, const char* cache_path, int64_t sample_quartets);
 
 /* ------------------------------------------------- allocation-free build */
 

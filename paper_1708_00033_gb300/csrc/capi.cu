@@ -271,6 +271,8 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
     // ------------------------------------------------------ Schwarz bounds
     TRY(X.Qall.alloc(sizeof(double) * npairs));
     HF_CUDA(cudaMemsetAsync(X.Qall.p, 0, sizeof(double) * npairs, st));
+    TRY(X.Bprim.alloc(sizeof(double) * npairs * X.maxpp));
+    HF_CUDA(cudaMemsetAsync(X.Bprim.p, 0, sizeof(double) * npairs * X.maxpp, st));
     std::vector<DevBuf> ids_all(kNumPairClasses);
     for (int c = 0; c < kNumPairClasses; c++) {
         if (!cnt_all[c]) continue;
@@ -286,9 +288,11 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
         sa.n = (int)cnt_all[c];
         sa.Q = X.Qall.as<double>();
         sa.boys64 = ctx->boys64.as<double>();
+        sa.Bprim = X.Bprim.as<double>();
         kEriClasses[ci].launch_schwarz(sa, kEriThreads, st);
         HF_CUDA(cudaGetLastError());
     }
+    KCHK(launch_sort_prims(npairs, S->pairs.as<PairHdr>(), X.Bprim.as<double>(), S->prims64.p, S->prims32.p, st));
     HF_CUDA(cudaMemsetAsync(X.counts.as<unsigned long long>() + 9, 0, sizeof(unsigned long long), st));
     KCHK(launch_copy_q(npairs, X.Qall.as<double>(), S->pairs.as<PairHdr>(), X.counts.as<unsigned long long>() + 9, st));
     unsigned long long qbits = 0;
@@ -361,6 +365,7 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
     TRY(X.staging_P.alloc(NN * sizeof(double)));
     TRY(X.staging_out.alloc(2 * NN * sizeof(double)));
     TRY(X.bad.alloc(sizeof(int)));
+    TRY(X.prim_count.alloc(sizeof(unsigned long long) * 2 * kNumClasses));
     HF_CUDA(cudaStreamSynchronize(st));
     HF_CUDA(cudaGetLastError());
     return HF_OK;
@@ -392,7 +397,7 @@ static int check_geometry_basis(const hf_geometry* g, const hf_basis* b, const h
     }
     if (th) {
         if (!(th->schwarz_tau >= 0.0) || !(th->fp32_cutoff >= 0.0)) return fail(HF_E_INVALID, "thresholds: negative");
-        if (th->prim_tau != 0.0) return fail(HF_E_UNSUPPORTED, "thresholds: prim_tau must be 0");
+        if (!(th->prim_tau >= 0.0)) return fail(HF_E_INVALID, "thresholds: negative prim_tau");
     }
     return HF_OK;
 }
@@ -519,6 +524,8 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
     a.Kt = S->Kt.as<double>();
     a.boys64 = ctx->boys64.as<double>();
     a.boys32 = ctx->boys32.as<float>();
+    a.prim_tau = S->th.prim_tau;
+    if (stats) HF_CUDA(cudaMemsetAsync(X.prim_count.p, 0, sizeof(unsigned long long) * 2 * kNumClasses, st));
     for (int ci = 0; ci < kNumClasses; ci++) {
         const auto& pl = S->plan[ci];
         const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
@@ -529,6 +536,7 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
         for (int prec = 0; prec < 2; prec++) {
             const long long n = prec ? pl.n32 : pl.n64;
             if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * ci + 2 * prec], st));
+            a.prim_count = stats ? X.prim_count.as<unsigned long long>() + 2 * ci + prec : nullptr;
             if (n > 0) {
                 a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
                 a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
@@ -559,20 +567,23 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
     HF_CUDA(cudaStreamSynchronize(st));
     HF_CUDA(cudaGetLastError());
     if (stats) {
+        unsigned long long pc[2 * kNumClasses];
+        HF_CUDA(cudaMemcpy(pc, X.prim_count.p, sizeof(pc), cudaMemcpyDeviceToHost));
         memset(stats, 0, sizeof(*stats));
         stats->quartets_unscreened = S->quartets_total;
-        const double pq = (double)X.maxpp * (double)X.maxpp;  // primitive quartets per shell quartet (upper bound)
         for (int ci = 0; ci < kNumClasses; ci++) {
             const auto& pl = S->plan[ci];
             stats->class_quartets_fp64[ci] = pl.n64;
             stats->class_quartets_fp32[ci] = pl.n32;
             stats->quartets_fp64 += pl.n64;
             stats->quartets_fp32 += pl.n32;
-            const double per = kEriClasses[ci].prim_flops * pq + kEriClasses[ci].cont_flops;
-            stats->class_flops_fp64[ci] = per * (double)pl.n64;
-            stats->class_flops_fp32[ci] = per * (double)pl.n32;
-            stats->flops_fp64 += per * (double)pl.n64;
-            stats->flops_fp32 += per * (double)pl.n32;
+            stats->prim_quartets_fp64 += (int64_t)pc[2 * ci];
+            stats->prim_quartets_fp32 += (int64_t)pc[2 * ci + 1];
+            const double pf = kEriClasses[ci].prim_flops, cf = kEriClasses[ci].cont_flops;
+            stats->class_flops_fp64[ci] = pf * (double)pc[2 * ci] + cf * (double)pl.n64;
+            stats->class_flops_fp32[ci] = pf * (double)pc[2 * ci + 1] + cf * (double)pl.n32;
+            stats->flops_fp64 += stats->class_flops_fp64[ci];
+            stats->flops_fp32 += stats->class_flops_fp32[ci];
             stats->kernels_launched += (pl.n64 > 0) + (pl.n32 > 0);
             if (timing) {
                 cudaEventElapsedTime(&stats->ms_class_fp64[ci], ctx->ev[4 * ci], ctx->ev[4 * ci + 1]);

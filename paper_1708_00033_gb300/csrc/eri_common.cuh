@@ -22,6 +22,7 @@ struct PrimPair {
     real PAx, PAy, PAz;  // P - A
     real K;              // c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p
     real oo2p;           // 1 / (2p)
+    real B;              // primitive-pair Schwarz bound sqrt(max |[ab|ab]|), normalised components
 };
 
 // Boys table: rows T_k = k / 32 for k = 0..kBoysRows-1 (T < 60); columns
@@ -138,6 +139,8 @@ constexpr int kEriThreads = 128;
         const real* P = (const real*)(sizeof(real) == 8 ? (const void*)a.P64 : (const void*)a.P32);                                  \
         const real* bt = (const real*)(sizeof(real) == 8 ? (const void*)a.boys64 : (const void*)a.boys32);  \
         const long long stride = (long long)gridDim.x * blockDim.x;                                          \
+        const real ptau = (real)a.prim_tau;                                                                  \
+        unsigned nprimq = 0;                                                                                 \
         for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_quartets; q += stride) { \
             const int b = find_bra(a.offsets, a.n_bra, q);                                                   \
             const int k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                            \
@@ -147,7 +150,11 @@ constexpr int kEriThreads = 128;
             if (hb.A == hb.B) f *= 0.5;                                                                      \
             if (hk.A == hk.B) f *= 0.5;                                                                      \
             if (a.same && b == k) f *= 0.5;                                                                  \
-            quartet_##NAME<real>(hb, hk, prims, bt, P, a.N, f, a.Jt, a.Kt, nullptr);                         \
+            nprimq += quartet_##NAME<real>(hb, hk, prims, bt, P, a.N, f, a.Jt, a.Kt, nullptr, ptau);         \
+        }                                                                                                    \
+        if (a.prim_count) {                                                                                  \
+            const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \
+            if ((threadIdx.x & 31) == 0 && w) atomicAdd(a.prim_count, w);                                    \
         }                                                                                                    \
     }                                                                                                        \
     void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s)              \
@@ -166,11 +173,57 @@ constexpr int kEriThreads = 128;
         if (t >= a.n) return;                                                                                \
         const int pid = a.ids[t];                                                                            \
         const PairHdr h = a.pairs[pid];                                                                      \
+        const PrimPair<double>* pr = (const PrimPair<double>*)a.prims64;                                     \
         double qm = 0.0;                                                                                     \
-        quartet_##NAME<double>(h, h, (const PrimPair<double>*)a.prims64, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm);          \
+        quartet_##NAME<double>(h, h, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm, 0.0);             \
         a.Q[pid] = sqrt(qm);                                                                                 \
+        for (int k = 0; k < h.nprim; k++) { /* bound of each primitive pair alone */                         \
+            PairHdr h1 = h;                                                                                  \
+            h1.prim0 = h.prim0 + k;                                                                          \
+            h1.nprim = 1;                                                                                    \
+            double qk = 0.0;                                                                                 \
+            quartet_##NAME<double>(h1, h1, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qk, 0.0);       \
+            a.Bprim[h.prim0 + k] = sqrt(qk);                                                                 \
+        }                                                                                                    \
     }                                                                                                        \
     void launch_schwarz_##NAME(const SchwarzArgs& a, int block, cudaStream_t s)                             \
     {                                                                                                        \
         if (a.n > 0) k_schwarz_##NAME<<<(a.n + block - 1) / block, block, 0, s>>>(a);                        \
+    }
+
+// Batched build: one persistent kernel per class over many molecules.  Warps
+// take chunks of the batch's quartet index space from a device counter (the
+// GPU analogue of the paper's dynamic load balancing, ddi_dlbnext); a quartet
+// index resolves to (molecule, bra, ket) by two binary searches.
+#define ERI_BATCH_KERNEL(NAME)                                                                               \
+    __global__ void __launch_bounds__(256) k_eri_batch_##NAME(const BatchArgs a)                            \
+    {                                                                                                        \
+        const int lane = threadIdx.x & 31;                                                                   \
+        const double ptau = a.prim_tau;                                                                      \
+        for (;;) {                                                                                           \
+            unsigned long long base = 0;                                                                     \
+            if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);                        \
+            base = __shfl_sync(0xffffffffu, base, 0);                                                        \
+            if (base >= (unsigned long long)a.n_total) break;                                                \
+            const long long end = min((long long)base + a.chunk, a.n_total);                                 \
+            for (long long q = (long long)base + lane; q < end; q += 32) {                                   \
+                const int m = find_bra(a.mol_off, a.n_mol, q);                                               \
+                const MolClass mc = a.mols[m];                                                               \
+                const long long ql = q - a.mol_off[m];                                                       \
+                const int b = find_bra(mc.offsets, mc.n_bra, ql);                                            \
+                const int k = (int)(ql - mc.offsets[b]);                                                     \
+                const PairHdr hb = mc.pairs[mc.bra[b]];                                                      \
+                const PairHdr hk = mc.pairs[mc.ket[k]];                                                      \
+                double f = 1.0;                                                                              \
+                if (hb.A == hb.B) f *= 0.5;                                                                  \
+                if (hk.A == hk.B) f *= 0.5;                                                                  \
+                if (mc.same && b == k) f *= 0.5;                                                             \
+                quartet_##NAME<double>(hb, hk, (const PrimPair<double>*)mc.prims64, a.boys64, mc.P64, mc.N, f, \
+                                       mc.Jt, mc.Kt, nullptr, ptau);                                         \
+            }                                                                                                \
+        }                                                                                                    \
+    }                                                                                                        \
+    void launch_eri_batch_##NAME(const BatchArgs& a, int grid, int block, cudaStream_t s)                   \
+    {                                                                                                        \
+        k_eri_batch_##NAME<<<grid, block, 0, s>>>(a);                                                        \
     }

@@ -376,20 +376,26 @@ def gen_class(X, Y):
                f"{len(targets)} [e0|f0] targets, {prim_flops} flops per primitive quartet, "
                f"{cnt.cont} per contracted quartet.")
     out.append(f"template <typename real>")
-    out.append(f"__device__ __forceinline__ void quartet_{name}(const PairHdr& hb, const PairHdr& hk,"
+    out.append(f"__device__ __forceinline__ int quartet_{name}(const PairHdr& hb, const PairHdr& hk,"
                f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
-    out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout)")
+    out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
+    out.append(f"    real ptau)")
     out.append("{")
+    out.append("    int nq = 0;")
+    out.append("    const real kB0 = prims[hk.prim0].B;")
     for l in acc_decl:
         out.append("    " + l)
     out.append("    for (int ib = 0; ib < hb.nprim; ib++) {")
     out.append("        const PrimPair<real> bp = prims[hb.prim0 + ib];")
+    out.append("        if (bp.B * kB0 < ptau) break;  // primitive pairs are sorted by B, descending")
     out.append("        const real bK = bp.K, bo2p = bp.oo2p;")
     for a in AX:
         if f"PA{a}" in used:
             out.append(f"        const real PA{a} = bp.PA{a};")
     out.append("        for (int ik = 0; ik < hk.nprim; ik++) {")
     out.append("            const PrimPair<real> kp = prims[hk.prim0 + ik];")
+    out.append("            if (bp.B * kp.B < ptau) break;")
+    out.append("            nq++;")
     for l in setup:
         out.append("            " + l)
     for l in vrr:
@@ -409,15 +415,17 @@ def gen_class(X, Y):
         for l in gen_schwarz(la, lb, xname):
             out.append("        " + l)
         out.append("        *qout = qmax;")
-    out.append("        return;")
+    out.append("        return nq;")
     out.append("    }")
     out.append("    const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
     out.append("    const real fj = (real)(4.0 * fscale), fk = (real)(2.0 * fscale);")
     for l in dig:
         out.append("    " + l)
+    out.append("    return nq;")
     out.append("}")
     out.append("")
     out.append(f"ERI_CLASS_KERNELS({name}, {X}, {Y})")
+    out.append(f"ERI_BATCH_KERNEL({name})")
     if X == Y:
         out.append(f"SCHWARZ_KERNEL({name})")
     info = dict(name=name, X=X, Y=Y, l=[la, lb, lc, ld], L=L, prim_flops=prim_flops, cont_flops=cnt.cont,
@@ -451,12 +459,14 @@ def main(outdir):
         lines.append(f"void launch_eri_{n}(const EriArgs&, int, int, int, cudaStream_t);")
         if info["X"] == info["Y"]:
             lines.append(f"void launch_schwarz_{n}(const SchwarzArgs&, int, cudaStream_t);")
+        lines.append(f"void launch_eri_batch_{n}(const BatchArgs&, int, int, cudaStream_t);")
     lines.append("")
     lines.append("const EriClassEntry kEriClasses[kNumClasses] = {")
     for info in infos:
         n = info["name"]
         lines.append(f"    {{{info['X']}, {info['Y']}, {info['L']}, {info['prim_flops']}, {info['cont_flops']}, "
-                     f"launch_eri_{n}, {('launch_schwarz_' + n) if info['X'] == info['Y'] else 'nullptr'}, \"{n}\"}},")
+                     f"launch_eri_{n}, {('launch_schwarz_' + n) if info['X'] == info['Y'] else 'nullptr'}, \"{n}\", "
+                     f"launch_eri_batch_{n}}},")
     lines.append("};")
     lines.append("}  // namespace hf")
     text = "\n".join(lines) + "\n"

@@ -43,6 +43,8 @@ struct EriArgs {
     double* Kt;
     const double* boys64;
     const float* boys32;
+    double prim_tau;                  // skip primitive quartets with B_ab * B_cd < prim_tau
+    unsigned long long* prim_count;   // evaluated primitive quartets (nullptr: not counted)
 };
 
 struct SchwarzArgs {
@@ -51,6 +53,34 @@ struct SchwarzArgs {
     const int* ids;       // pair ids of one diagonal class
     int n;
     double* Q;            // [pair id] output bound
+    const double* boys64;
+    double* Bprim;        // [primitive pair] output bound of each primitive pair
+};
+
+// One molecule's view of one class in a batched build.
+struct MolClass {
+    const PairHdr* pairs;
+    const void* prims64;
+    const int* bra;
+    const int* ket;
+    const long long* offsets;  // [n_bra + 1]
+    int n_bra;
+    int same;
+    int N;
+    int pad;
+    const double* P64;
+    double* Jt;
+    double* Kt;
+};
+
+struct BatchArgs {
+    const MolClass* mols;        // [n_mol]
+    const long long* mol_off;    // [n_mol + 1] exclusive prefix of this class's quartets per molecule
+    int n_mol;
+    int chunk;                   // quartets per work-queue grab (per warp)
+    long long n_total;
+    unsigned long long* counter; // work-queue head, zero at launch
+    double prim_tau;
     const double* boys64;
 };
 
@@ -61,6 +91,7 @@ struct EriClassEntry {
     void (*launch)(const EriArgs&, int use_f32, int grid, int block, cudaStream_t);
     void (*launch_schwarz)(const SchwarzArgs&, int block, cudaStream_t);
     const char* name;
+    void (*launch_batch)(const BatchArgs&, int grid, int block, cudaStream_t);
 };
 extern const EriClassEntry kEriClasses[kNumClasses];
 
@@ -133,6 +164,6 @@ struct hf_system {
     int64_t quartets_total = 0;
     // scratch
     hf::DevBuf class_q[hf::kNumPairClasses];  // sorted bounds of class_ids
-    hf::DevBuf Qall, counts, staging_P, staging_out, bad;
+    hf::DevBuf Qall, counts, staging_P, staging_out, bad, Bprim, prim_count;
     int maxpp = 0;
 };

@@ -125,6 +125,7 @@ extern "C" int hf_fock_build_noalloc(hf_system* S, const double* P, double* F, d
     a.Kt = sc->Kt;
     a.boys64 = ctx->boys64.as<double>();
     a.boys32 = ctx->boys32.as<float>();
+    a.prim_tau = S->th.prim_tau;
     for (int ci = 0; ci < kNumClasses; ci++) {
         const auto& pl = S->plan[ci];
         const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;

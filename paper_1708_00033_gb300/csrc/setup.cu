@@ -253,6 +253,41 @@ int bitonic_sort_desc(double* key, int* val, int n, int n_pad, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Attach the primitive-pair bounds and order each pair's primitive pairs by
+// bound, largest first, so that the ERI loops can stop at the first
+// primitive quartet whose bound product falls below the primitive threshold.
+__global__ void k_sort_prims(long long n_pairs, const PairHdr* __restrict__ pairs, const double* __restrict__ Bprim,
+                             PrimPair<double>* __restrict__ p64, PrimPair<float>* __restrict__ p32)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_pairs) return;
+    const int o = pairs[t].prim0, n = pairs[t].nprim;
+    for (int k = 0; k < n; k++) {
+        p64[o + k].B = Bprim[o + k];
+        p32[o + k].B = (float)Bprim[o + k];
+    }
+    for (int i = 1; i < n; i++) {  // insertion sort, descending B
+        const PrimPair<double> r = p64[o + i];
+        const PrimPair<float> f = p32[o + i];
+        int j = i - 1;
+        while (j >= 0 && p64[o + j].B < r.B) {
+            p64[o + j + 1] = p64[o + j];
+            p32[o + j + 1] = p32[o + j];
+            j--;
+        }
+        p64[o + j + 1] = r;
+        p32[o + j + 1] = f;
+    }
+}
+
+int launch_sort_prims(long long n_pairs, const PairHdr* pairs, const double* Bprim, void* p64, void* p32, cudaStream_t s)
+{
+    if (n_pairs > 0)
+        k_sort_prims<<<(unsigned)((n_pairs + 127) / 128), 128, 0, s>>>(n_pairs, pairs, Bprim, (PrimPair<double>*)p64,
+                                                                     (PrimPair<float>*)p32);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // ------------------------------------------------------- quartet schedule --
 // For bra b of class X: kets of class Y (sorted by Q descending) with
 // Q_b Q_k >= tau form a prefix; when X == Y only kets k <= b are unique.

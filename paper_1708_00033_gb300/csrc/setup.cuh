@@ -19,6 +19,7 @@ int launch_copy_q(long long n, const double* Q, PairHdr* pairs, unsigned long lo
 int launch_class_scatter_sig(long long n, const int* pclass, const double* Q, int X, double qmax, double tau,
                              unsigned* cursor, double* key, int* val, cudaStream_t s);
 int bitonic_sort_desc(double* key, int* val, int n, int n_pad, cudaStream_t s);
+int launch_sort_prims(long long n_pairs, const PairHdr* pairs, const double* Bprim, void* p64, void* p32, cudaStream_t s);
 int launch_ket_counts(int n_bra, const double* qb, int n_ket, const double* qk, int same, double tau, double cutoff,
                       long long* c64, long long* c32, int* kstart32, cudaStream_t s);
 int launch_scan(int n, const long long* in, long long* out, cudaStream_t s);

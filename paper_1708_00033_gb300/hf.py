@@ -64,7 +64,8 @@ class Stats_c(ctypes.Structure):
                 ("ms_class_fp64", ctypes.c_float * NUM_CLASSES), ("ms_class_fp32", ctypes.c_float * NUM_CLASSES),
                 ("ms_eri", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("class_flops_fp64", ctypes.c_double * NUM_CLASSES), ("class_flops_fp32", ctypes.c_double * NUM_CLASSES),
-                ("kernels_launched", ctypes.c_int32)]
+                ("kernels_launched", ctypes.c_int32), ("prim_quartets_fp64", ctypes.c_int64),
+                ("prim_quartets_fp32", ctypes.c_int64)]
 
 
 class SystemInfo_c(ctypes.Structure):
@@ -73,6 +74,29 @@ class SystemInfo_c(ctypes.Structure):
                 ("quartets_unscreened", ctypes.c_int64), ("quartets_fp64", ctypes.c_int64),
                 ("quartets_fp32", ctypes.c_int64), ("E_nn", ctypes.c_double), ("Q_max", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64)]
+
+
+class ScfOpts_c(ctypes.Structure):
+    _fields_ = [("n_occ", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("e_tol", ctypes.c_double),
+                ("d_tol", ctypes.c_double), ("diis_size", ctypes.c_int32), ("diis_off", ctypes.c_int32)]
+
+
+class ScfResult_c(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("E_nn", ctypes.c_double), ("iterations", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("last_dE", ctypes.c_double), ("last_dP", ctypes.c_double),
+                ("seconds_total", ctypes.c_double), ("seconds_fock", ctypes.c_double),
+                ("seconds_diag", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int32), ("n_kept", ctypes.c_int32),
+                ("s_min", ctypes.c_double)]
+
+
+class BatchInfo_c(ctypes.Structure):
+    _fields_ = [("n_mol", ctypes.c_int32), ("packed_len", ctypes.c_int64), ("n_bf_total", ctypes.c_int64),
+                ("quartets", ctypes.c_int64), ("class_quartets", ctypes.c_int64 * NUM_CLASSES),
+                ("block", ctypes.c_int32 * NUM_CLASSES), ("chunk", ctypes.c_int32 * NUM_CLASSES),
+                ("blocks_per_sm", ctypes.c_int32 * NUM_CLASSES)]
+
+
+HF_BATCH_SEQUENTIAL = 4
 
 
 class HFError(RuntimeError):
@@ -110,6 +134,18 @@ def load_library():
     lib.hf_fock_build.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Stats_c),
                                   ctypes.c_int]
     lib.hf_fock_build_noalloc.argtypes = [vp, vp, vp, vp, vp]
+    lib.hf_scf_run.argtypes = [vp, ctypes.POINTER(ScfOpts_c), vp, vp, vp, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ScfResult_c), ctypes.c_int]
+    lib.hf_eigh.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_int]
+    lib.hf_batch_create.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Geometry_c), ctypes.POINTER(Basis_c),
+                                    ctypes.POINTER(Thresholds_c), ctypes.POINTER(vp)]
+    lib.hf_batch_destroy.argtypes = [vp]
+    lib.hf_batch_destroy.restype = None
+    lib.hf_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo_c)]
+    lib.hf_batch_offsets.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.hf_fock_build_batch.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float),
+                                        ctypes.c_int]
+    lib.hf_batch_tune.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
     _lib = lib
     return lib
 
@@ -164,7 +200,7 @@ class System:
     """hf_system_create: one molecule with its screening plan."""
 
     def __init__(self, ctx: Context, geom: _inputs.Geometry, basis: _inputs.Basis, schwarz_tau: float = 0.0,
-                 fp32_cutoff: float = 0.0):
+                 fp32_cutoff: float = 0.0, prim_tau: float = 0.0):
         self.ctx = ctx
         Z, xyz = _as_i32(geom.Z), _as_f64(geom.xyz)
         at, l, npr = _as_i32(basis.atom), _as_i32(basis.l), _as_i32(basis.nprim)
@@ -172,7 +208,7 @@ class System:
         g = Geometry_c(int(Z.shape[0]), Z.ctypes.data_as(_i32p), xyz.ctypes.data_as(_f64p))
         b = Basis_c(int(l.shape[0]), at.ctypes.data_as(_i32p), l.ctypes.data_as(_i32p), npr.ctypes.data_as(_i32p),
                     ex.ctypes.data_as(_f64p), co.ctypes.data_as(_f64p))
-        th = Thresholds_c(float(schwarz_tau), float(fp32_cutoff), 0.0)
+        th = Thresholds_c(float(schwarz_tau), float(fp32_cutoff), float(prim_tau))
         self._h = ctypes.c_void_p()
         _check(load_library().hf_system_create(ctx._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(th),
                                                ctypes.byref(self._h)), "hf_system_create")
@@ -254,6 +290,99 @@ class System:
         if stats or timing:
             out["stats"] = stats_dict(st)
         return out
+
+
+class Batch:
+    """hf_batch_create: many molecules built together in one graph-captured step."""
+
+    def __init__(self, ctx: Context, geoms, bases, schwarz_tau: float = 0.0, prim_tau: float = 0.0):
+        self.ctx = ctx
+        n = len(geoms)
+        keep = []
+        G = (Geometry_c * n)()
+        Bs = (Basis_c * n)()
+        for m, (g, b) in enumerate(zip(geoms, bases)):
+            arrs = [_as_i32(g.Z), _as_f64(g.xyz), _as_i32(b.atom), _as_i32(b.l), _as_i32(b.nprim), _as_f64(b.exps),
+                    _as_f64(b.coefs)]
+            keep.append(arrs)
+            G[m] = Geometry_c(int(arrs[0].shape[0]), arrs[0].ctypes.data_as(_i32p), arrs[1].ctypes.data_as(_f64p))
+            Bs[m] = Basis_c(int(arrs[3].shape[0]), arrs[2].ctypes.data_as(_i32p), arrs[3].ctypes.data_as(_i32p),
+                            arrs[4].ctypes.data_as(_i32p), arrs[5].ctypes.data_as(_f64p), arrs[6].ctypes.data_as(_f64p))
+        th = Thresholds_c(float(schwarz_tau), 0.0, float(prim_tau))
+        self._h = ctypes.c_void_p()
+        _check(load_library().hf_batch_create(ctx._h, n, G, Bs, ctypes.byref(th), ctypes.byref(self._h)),
+               "hf_batch_create")
+        self.n_mol = n
+        off = (ctypes.c_int64 * (n + 1))()
+        _check(load_library().hf_batch_offsets(self._h, off), "hf_batch_offsets")
+        self.offsets = np.array(list(off), dtype=np.int64)
+        self.n_bf = [int(np.sqrt(self.offsets[m + 1] - self.offsets[m]) + 0.5) for m in range(n)]
+
+    def info(self) -> dict:
+        inf = BatchInfo_c()
+        _check(load_library().hf_batch_get_info(self._h, ctypes.byref(inf)), "hf_batch_get_info")
+        d = {k: getattr(inf, k) for k, _ in BatchInfo_c._fields_}
+        for k in ("class_quartets", "block", "chunk", "blocks_per_sm"):
+            d[k] = list(d[k])
+        return d
+
+    def tune(self, cache_path: str | None = None, sample_quartets: int = 0):
+        _check(load_library().hf_batch_tune(self._h, cache_path.encode() if cache_path else None,
+                                            int(sample_quartets)), "hf_batch_tune")
+
+    def fock_build(self, P, F, energies: bool = False, sequential: bool = False):
+        """Packed P in, packed F out (CUDA tensors or numpy arrays); returns (ms, E_elec or None)."""
+        is_dev = hasattr(P, "is_cuda") and P.is_cuda
+        flags = (HF_PTR_DEVICE if is_dev else 0) | (HF_BATCH_SEQUENTIAL if sequential else 0)
+        ptr = (lambda t: t.data_ptr()) if is_dev else (lambda a: a.ctypes.data)
+        E = np.zeros(self.n_mol) if energies else None
+        ms = ctypes.c_float(0.0)
+        _check(load_library().hf_fock_build_batch(self._h, ptr(P), ptr(F), E.ctypes.data_as(_f64p) if energies else None,
+                                                  ctypes.byref(ms), flags), "hf_fock_build_batch")
+        return ms.value, E
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().hf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scf(system: "System", n_occ: int = 0, max_iter: int = 100, e_tol: float = 1e-9, d_tol: float = 1e-6,
+        diis_size: int = 8, P_guess=None, raise_on_noconv: bool = True) -> dict:
+    """hf_scf_run with host arrays; returns energy, density, orbital energies and timings."""
+    N = system.n_bf
+    o = ScfOpts_c(int(n_occ), int(max_iter), float(e_tol), float(d_tol), int(diis_size), 1 if diis_size == 0 else 0)
+    P_out = np.empty((N, N))
+    eps = np.zeros(N)
+    en = np.zeros(max_iter)
+    res = ScfResult_c()
+    Pg = None if P_guess is None else _as_f64(P_guess)
+    rc = load_library().hf_scf_run(system._h, ctypes.byref(o), Pg.ctypes.data if Pg is not None else None,
+                                   P_out.ctypes.data, eps.ctypes.data, en.ctypes.data_as(_f64p), ctypes.byref(res),
+                                   HF_PTR_HOST)
+    if rc != HF_E_NOCONV or raise_on_noconv:
+        _check(rc, "hf_scf_run")
+    out = {k: getattr(res, k) for k, _ in ScfResult_c._fields_}
+    out.update(P=P_out, eps=eps[: res.n_kept], energies=en[: res.iterations].copy(), status=rc)
+    return out
+
+
+def eigh(ctx: Context, A) -> tuple:
+    """hf_eigh on a host matrix: eigenvalues ascending and eigenvectors as columns."""
+    A = _as_f64(A)
+    n = A.shape[0]
+    w = np.empty(n)
+    V = np.empty((n, n))
+    _check(load_library().hf_eigh(ctx._h, n, A.ctypes.data, w.ctypes.data, V.ctypes.data, HF_PTR_HOST), "hf_eigh")
+    return w, V
 
 
 def fock_build_noalloc(system: "System", P, F, J=None, K=None):

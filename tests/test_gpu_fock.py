@@ -141,3 +141,22 @@ def test_unsupported_basis_is_rejected(ctx):
     with pytest.raises(hf.HFError) as e:
         hf.System(ctx, geom, basis)
     assert e.value.code == hf.HF_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prim_tau", [1e-15, 1e-13])
+def test_primitive_screening_parity(ctx, oracle_mod, prim_tau):
+    """Primitive-pair Schwarz screening changes each integral by at most prim_tau
+    per skipped primitive quartet; F must stay within the FP64 tolerance."""
+    geom = I.water_cluster(6, 2, 11)
+    basis = I.synthetic_basis(geom)
+    mol = oracle_mod.Molecule(geom, basis)
+    P = _density(oracle_mod, mol, 30, 2, 11)
+    tau = 1e-10
+    J, K = mol.jk_unique(P, tau)
+    from paper_1708_00033_gb300 import hf
+    s = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=prim_tau)
+    out = s.fock_build(P, want_J=True, want_K=True, stats=True)
+    st = out["stats"]
+    assert st["prim_quartets_fp64"] < 81 * st["quartets_fp64"]
+    assert np.abs(out["J"] - J).max() <= 1e-10
+    assert np.abs(out["K"] - K).max() <= 1e-10

@@ -1,0 +1,94 @@
+"""GPU SCF (orthogonalisation, Jacobi eigensolver, DIIS, density formation)
+against the oracle's SCF and against invariants that hold at any size."""
+import numpy as np
+import pytest
+
+from paper_1708_00033_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1708_00033_gb300 import hf
+    return hf.Context(0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 257, 600])
+def test_eigh_vs_library_routine(ctx, n):
+    from paper_1708_00033_gb300 import hf
+    rng = np.random.default_rng(n)
+    G = rng.standard_normal((n, n))
+    A = G + G.T
+    A[0, 0] += 3.0
+    w, V = hf.eigh(ctx, A)
+    w_ref = np.linalg.eigvalsh(A)
+    scale = np.abs(w_ref).max()
+    assert np.abs(w - w_ref).max() <= 1e-12 * scale
+    assert np.abs(A @ V - V * w).max() <= 1e-11 * scale
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-12
+
+
+def test_eigh_degenerate_and_diagonal(ctx):
+    from paper_1708_00033_gb300 import hf
+    A = np.diag([3.0, 1.0, 1.0, -2.0, 5.0, 1.0])
+    w, V = hf.eigh(ctx, A)
+    assert np.allclose(w, [-2.0, 1.0, 1.0, 1.0, 3.0, 5.0], atol=1e-15)
+    assert np.abs(A @ V - V * w).max() < 1e-14
+
+
+def test_scf_h2_textbook(ctx, oracle_mod):
+    from paper_1708_00033_gb300 import hf
+    geom, basis = I.h2_sto3g(1.4)
+    s = hf.System(ctx, geom, basis)
+    r = hf.scf(s, e_tol=1e-12, d_tol=1e-10)
+    assert r["converged"]
+    ref = oracle_mod.scf(oracle_mod.Molecule(geom, basis), e_tol=1e-12, d_tol=1e-10)
+    assert abs(r["energy"] - ref.energy) < 1e-10
+    assert abs(r["energy"] - (-1.1167)) <= 0.5e-4
+
+
+@pytest.mark.parametrize("nw,seed", [(1, 2), (2, 4)])
+def test_scf_vs_oracle(ctx, oracle_mod, nw, seed):
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(nw, 2, seed)
+    basis = I.synthetic_basis(geom)
+    s = hf.System(ctx, geom, basis)
+    r = hf.scf(s, e_tol=1e-11, d_tol=1e-8)
+    ref = oracle_mod.scf(oracle_mod.Molecule(geom, basis), e_tol=1e-11, d_tol=1e-8)
+    assert r["converged"] and ref.converged
+    assert abs(r["energy"] - ref.energy) < 1e-9
+    assert np.abs(r["P"] - ref.P).max() < 1e-6
+    assert np.abs(r["eps"][: len(ref.eps)] - ref.eps).max() < 1e-6
+
+
+def test_scf_invariants_sixteen_waters(ctx):
+    """400 basis functions, Schwarz 1e-10: properties any converged closed-shell SCF has."""
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(16, 2, 0)
+    basis = I.synthetic_basis(geom)
+    s = hf.System(ctx, geom, basis, schwarz_tau=1e-10)
+    r = hf.scf(s)
+    assert r["converged"]
+    S, H = s.one_electron()
+    P = r["P"]
+    n_el = int(geom.Z.sum())
+    assert abs(np.trace(P @ S) - n_el) < 1e-8
+    assert np.abs(P @ S @ P - 2.0 * P).max() < 1e-6  # idempotency of the total density
+    F = s.fock_build(P)["F"]
+    comm = F @ P @ S - S @ P @ F
+    assert np.abs(comm).max() < 1e-4
+    assert r["energy"] <= r["energies"][0] + 1e-10  # below the core-guess iteration
+    assert np.all(np.diff(r["eps"]) >= -1e-12)
+
+
+def test_scf_reports_nonconvergence(ctx):
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(2, 2, 4)
+    basis = I.synthetic_basis(geom)
+    s = hf.System(ctx, geom, basis)
+    r = hf.scf(s, max_iter=2, raise_on_noconv=False)
+    assert r["status"] == hf.HF_E_NOCONV and not r["converged"] and r["iterations"] == 2
