@@ -149,6 +149,7 @@ __global__ void k_build_pairs(long long n_pairs, int maxpp, const int* __restric
             r.PAz = r.Pz - Az;
             r.K = ca * cb * exp(-a * b * ip * R2) * c52 * ip;
             r.oo2p = 0.5 * ip;
+            r.B = 0.0;  // set by the Schwarz pass; 0 never stops a primitive loop whose threshold is 0
             p64[t * maxpp + k] = r;
             PrimPair<float> f;
             f.p = (float)r.p;
@@ -160,6 +161,7 @@ __global__ void k_build_pairs(long long n_pairs, int maxpp, const int* __restric
             f.PAz = (float)r.PAz;
             f.K = (float)r.K;
             f.oo2p = (float)r.oo2p;
+            f.B = 0.0f;
             p32[t * maxpp + k] = f;
         }
     }
