@@ -44,13 +44,21 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
-    return ap.parse_args()
+    ap.add_argument("--prim-tau", type=float, default=1e-14)
+    ap.add_argument("--mode", default="fock", choices=["fock", "scf", "mixed", "batch"])
+    ap.add_argument("--n-mol", type=int, default=512)
+    a = ap.parse_args()
+    if a.mode == "mixed" and "--waters" not in sys.argv:
+        a.waters, a.config_id = 256, 3
+    if a.mode == "mixed" and "--fp32-cutoff" not in sys.argv:
+        a.fp32_cutoff = 1e-4
+    return a
 
 
 def workload_name(a):
     prec = "FP64" if a.fp32_cutoff <= 0 else f"mixed FP32<{a.fp32_cutoff:g}"
     return (f"{a.waters}-water cluster, {25 * a.waters} Cartesian BF, synthetic 3-primitive basis, "
-            f"Schwarz tau={a.tau:g}, {prec} Fock build (J+K)")
+            f"Schwarz tau={a.tau:g}, primitive tau={a.prim_tau:g}, {prec} Fock build (J+K)")
 
 
 def dist_env():
@@ -136,7 +144,7 @@ def run_ours(a):
     geom = inputs.water_cluster(a.waters, a.config_id, rank)
     basis = inputs.synthetic_basis(geom)
     ctx = hf.Context(local)
-    sysm = hf.System(ctx, geom, basis, schwarz_tau=a.tau, fp32_cutoff=a.fp32_cutoff)
+    sysm = hf.System(ctx, geom, basis, schwarz_tau=a.tau, fp32_cutoff=a.fp32_cutoff, prim_tau=a.prim_tau)
     N = sysm.n_bf
     S, _ = sysm.one_electron()
     n_occ = inputs.n_electrons(geom) // 2
@@ -199,7 +207,7 @@ def run_ours(a):
     fl = stats[0]["class_flops_fp64"][c] + stats[0]["class_flops_fp32"][c]
     achieved = fl / (ms_cls[c] / 1e3) / 1e9
     eri_ms = float(np.mean([s["ms_eri"] for s in stats]))
-    eri_gflops = stats[0]["flops_fp64"] / (eri_ms / 1e3) / 1e9
+    eri_gflops = (stats[0]["flops_fp64"] + stats[0]["flops_fp32"]) / (eri_ms / 1e3) / 1e9
     line = {
         "metric": "Fock builds/s",
         "value": value,
@@ -214,8 +222,11 @@ def run_ours(a):
         "dtype": "f64" if a.fp32_cutoff <= 0 else "f64+f32",
         "data": "synthetic",
         "config": {"workload": workload_name(a), "waters": a.waters, "n_bf": N, "schwarz_tau": a.tau,
-                   "fp32_cutoff": a.fp32_cutoff, "density": "random S-orthonormal C, n_occ=%d" % n_occ,
+                   "prim_tau": a.prim_tau, "fp32_cutoff": a.fp32_cutoff,
+                   "density": "random S-orthonormal C, n_occ=%d" % n_occ,
                    "quartets_evaluated": stats[0]["quartets_fp64"] + stats[0]["quartets_fp32"],
+                   "quartets_fp32": stats[0]["quartets_fp32"],
+                   "primitive_quartets": stats[0]["prim_quartets_fp64"] + stats[0]["prim_quartets_fp32"],
                    "quartets_unscreened": stats[0]["quartets_unscreened"],
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "gpu_launches": int(sum(s["kernels_launched"] for s in stats)),
@@ -300,10 +311,144 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def _scf_run(hf, sysm, **kw):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = hf.scf(sysm, **kw)
+    torch.cuda.synchronize()
+    r["wall_s"] = time.perf_counter() - t0
+    return r
+
+
+def run_scf(a):
+    """SCF time to a converged energy: plain FP64 vs mixed-then-FP64 builds (one step = one SCF)."""
+    from paper_1708_00033_gb300 import hf, inputs
+    geom = inputs.water_cluster(a.waters, a.config_id, 0)
+    basis = inputs.synthetic_basis(geom)
+    ctx = hf.Context(0)
+    out = {}
+    for name, cut in (("fp64", 0.0), ("mixed", 1e-4)):
+        t0 = time.perf_counter()
+        sysm = hf.System(ctx, geom, basis, schwarz_tau=a.tau, prim_tau=a.prim_tau, fp32_cutoff=cut)
+        setup = time.perf_counter() - t0
+        r = _scf_run(hf, sysm, e_tol=1e-9, d_tol=1e-6)
+        out[name] = {"energy": r["energy"], "iterations": r["iterations"], "mixed_iterations": r["mixed_iterations"],
+                     "scf_s": r["wall_s"], "setup_s": setup, "total_s": r["wall_s"] + setup,
+                     "fock_s": r["seconds_fock"], "diag_s": r["seconds_diag"], "jacobi_sweeps": r["jacobi_sweeps"],
+                     "energies": [float(x) for x in r["energies"]]}
+        del sysm
+    dE = abs(out["mixed"]["energy"] - out["fp64"]["energy"])
+    line = {"metric": "SCF time to converged energy (|dE|<1e-9, RMS dP<1e-6)", "value": out["fp64"]["total_s"],
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{a.waters}-water cluster SCF, core-Hamiltonian guess", "schwarz_tau": a.tau,
+                       "prim_tau": a.prim_tau},
+            "variants": out, "mixed_vs_fp64_energy_diff": dE,
+            "mixed_speedup": out["fp64"]["total_s"] / out["mixed"]["total_s"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_mixed(a):
+    """One mixed-precision build vs one FP64 build of the same cluster."""
+    import numpy as np
+    import torch
+    from paper_1708_00033_gb300 import hf, inputs
+    geom = inputs.water_cluster(a.waters, a.config_id, 0)
+    basis = inputs.synthetic_basis(geom)
+    ctx = hf.Context(0)
+    res = {}
+    Pd = None
+    for name, cut in (("mixed", a.fp32_cutoff), ("fp64", 0.0)):
+        t0 = time.perf_counter()
+        sysm = hf.System(ctx, geom, basis, schwarz_tau=a.tau, prim_tau=a.prim_tau, fp32_cutoff=cut)
+        setup = time.perf_counter() - t0
+        if Pd is None:
+            S, _ = sysm.one_electron()
+            P = random_density(S, inputs.n_electrons(geom) // 2, a.config_id, 0)
+            Pd = torch.from_numpy(P).cuda()
+            del S
+        Fd = torch.empty_like(Pd)
+        sysm.fock_build(Pd, F=Fd)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = sysm.fock_build(Pd, F=Fd, timing=True)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = {"ms": e0.elapsed_time(e1), "E_elec": out["E_elec"], "stats": out["stats"], "setup_s": setup,
+                     "F": Fd.clone()}
+        del sysm
+    st = res["mixed"]["stats"]
+    dF = float((res["mixed"]["F"] - res["fp64"]["F"]).abs().max())
+    n32 = st["quartets_fp32"]
+    line = {"metric": "Fock builds/s", "value": 1e3 / res["mixed"]["ms"], "unit": "Fock builds/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": 1, "warmup": 1, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "fp32_cutoff": a.fp32_cutoff},
+            "fp64_builds_per_s": 1e3 / res["fp64"]["ms"], "speedup_vs_fp64": res["fp64"]["ms"] / res["mixed"]["ms"],
+            "abs_dE_vs_fp64_gpu": abs(res["mixed"]["E_elec"] - res["fp64"]["E_elec"]), "max_abs_dF_vs_fp64_gpu": dF,
+            "fp32_quartet_fraction": n32 / max(1, n32 + st["quartets_fp64"]),
+            "ms": {k: v["ms"] for k, v in res.items()}, "setup_s": {k: v["setup_s"] for k, v in res.items()},
+            "flops": {"fp64": st["flops_fp64"], "fp32": st["flops_fp32"]},
+            "class_ms_fp32": [round(x, 2) for x in st["ms_class_fp32"]],
+            "class_ms_fp64": [round(x, 2) for x in st["ms_class_fp64"]]}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(a):
+    """512 independent clusters of 1..16 waters: graph-captured batched builds vs per-molecule launches."""
+    import numpy as np
+    import torch
+    from paper_1708_00033_gb300 import hf, inputs
+    ctx = hf.Context(0)
+    geoms = [inputs.batch_cluster(inputs.CONFIG_BATCH, m) for m in range(a.n_mol)]
+    bases = [inputs.synthetic_basis(g) for g in geoms]
+    t0 = time.perf_counter()
+    batch = hf.Batch(ctx, geoms, bases, schwarz_tau=a.tau, prim_tau=a.prim_tau)
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batch.tune(os.path.join(tempfile.gettempdir(), "hf_batch_tune.txt"), sample_quartets=500000)
+    tune_s = time.perf_counter() - t0
+    rng = np.random.default_rng(4)
+    P = np.zeros(int(batch.offsets[-1]))
+    for m, n in enumerate(batch.n_bf):
+        G = rng.standard_normal((n, max(1, n // 5)))
+        P[batch.offsets[m]:batch.offsets[m + 1]] = (0.2 * G @ G.T).ravel()
+    Pd = torch.from_numpy(P).cuda()
+    F = torch.empty_like(Pd)
+    for _ in range(a.warmup):
+        batch.fock_build(Pd, F)
+    ms_graph = [batch.fock_build(Pd, F)[0] for _ in range(a.steps)]
+    Fs = torch.empty_like(Pd)
+    batch.fock_build(Pd, Fs, sequential=True)
+    ms_seq = [batch.fock_build(Pd, Fs, sequential=True)[0] for _ in range(max(1, a.steps // 2))]
+    dF = float((F - Fs).abs().max())
+    info = batch.info()
+    g = sum(ms_graph) / len(ms_graph)
+    s = sum(ms_seq) / len(ms_seq)
+    line = {"metric": "Fock builds/s", "value": a.n_mol / (g / 1e3), "unit": "molecule Fock builds/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{a.n_mol} clusters of U{{1..16}} waters (seeds (4,m)), Schwarz tau={a.tau:g}, "
+                                   f"primitive tau={a.prim_tau:g}", "n_bf_total": info["n_bf_total"],
+                       "quartets": info["quartets"]},
+            "graph_ms": g, "sequential_ms": s, "sequential_builds_per_s": a.n_mol / (s / 1e3),
+            "speedup_vs_per_molecule_launches": s / g, "max_abs_dF_graph_vs_sequential": dF,
+            "setup_s": setup, "tune_s": tune_s,
+            "tuned": {"block": info["block"], "chunk": info["chunk"], "blocks_per_sm": info["blocks_per_sm"]}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode == "scf":
+        run_scf(a)
+    elif a.mode == "mixed":
+        run_mixed(a)
+    elif a.mode == "batch":
+        run_batch(a)
     else:
         run_ours(a)
 

@@ -52,6 +52,7 @@ extern "C" {
 #define HF_PTR_HOST 0   /* matrix arguments are host pointers */
 #define HF_PTR_DEVICE 1 /* matrix arguments are device pointers */
 #define HF_TIMING 2     /* fill the per-kernel device times of hf_stats */
+#define HF_FP64_ONLY 8  /* hf_fock_build: evaluate the FP32 part of a mixed system in FP64 too */
 
 typedef struct hf_ctx hf_ctx;       /* one device + one stream + constant tables */
 typedef struct hf_system hf_system; /* one molecule: basis, pairs, screening plan, 1e matrices */
@@ -194,7 +195,12 @@ int hf_fock_build(hf_system* sys, const double* P, double* F, double* J, double*
  *   e_tol      |E_k - E_{k-1}| threshold in Eh (0: 1e-9)
  *   d_tol      RMS(P_k - P_{k-1}) threshold (0: 1e-6)
  *   diis_size  Pulay DIIS history length, 0..16 (0 with diis_off = 1 disables)
- *   diis_off   1 disables DIIS */
+ *   diis_off   1 disables DIIS
+ *   mixed_switch  for a system with fp32_cutoff > 0: Fock builds use the
+ *              mixed FP32/FP64 split until |dE| < mixed_switch (0: 1e-5),
+ *              then every later build is FP64 only (HF_FP64_ONLY) and the
+ *              DIIS history restarts; convergence is only declared on FP64
+ *              builds, so the final energy is that of the plain FP64 method. */
 typedef struct {
     int32_t n_occ;
     int32_t max_iter;
@@ -202,6 +208,7 @@ typedef struct {
     double d_tol;
     int32_t diis_size;
     int32_t diis_off;
+    double mixed_switch;
 } hf_scf_opts;
 
 /* Result of hf_scf_run. */
@@ -217,6 +224,8 @@ typedef struct {
     int32_t jacobi_sweeps;  /* total Jacobi sweeps of all diagonalisations */
     int32_t n_kept;         /* orthogonal basis size (N unless near-linear dependence) */
     double s_min;           /* smallest overlap eigenvalue */
+    int32_t mixed_iterations; /* builds done with the FP32/FP64 split */
+    int32_t pad;
 } hf_scf_result;
 
 /* Closed-shell SCF (Section 3, Eq. FC = eSC): X = S^-1/2 (canonical

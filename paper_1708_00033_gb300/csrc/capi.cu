@@ -543,7 +543,8 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
                 a.n_quartets = n;
                 const long long blocks = (n + kEriThreads - 1) / kEriThreads;
                 const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
-                kEriClasses[ci].launch(a, prec, grid, kEriThreads, st);
+                const int use_f32 = prec && !(flags & HF_FP64_ONLY);
+                kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st);
                 HF_CUDA(cudaGetLastError());
             }
             if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * ci + 2 * prec + 1], st));

@@ -128,7 +128,10 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
         if (o.d_tol == 0.0) o.d_tol = 1e-6;
         if (o.diis_size == 0 && !o.diis_off) o.diis_size = 8;
         if (o.diis_off) o.diis_size = 0;
+        if (o.mixed_switch == 0.0) o.mixed_switch = 1e-5;
     }
+    if (!opts_in) o.mixed_switch = 1e-5;
+    bool mixed = S->th.fp32_cutoff > 0.0;
     const int N = S->n_bf;
     const int n_occ = o.n_occ > 0 ? o.n_occ : S->n_electrons / 2;
     if (n_occ <= 0 || n_occ > N) return scf_fail(HF_E_INVALID, "hf_scf_run: occupied orbital count out of range");
@@ -238,11 +241,13 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
         double E_el = 0.0;
         const double tf = now_s();
         double* Fslot = Fh[head].as<double>();
-        int rc = hf_fock_build(S, P.as<double>(), Fslot, nullptr, nullptr, &E_el, nullptr, HF_PTR_DEVICE);
+        int rc = hf_fock_build(S, P.as<double>(), Fslot, nullptr, nullptr, &E_el, nullptr,
+                               HF_PTR_DEVICE | (mixed ? 0 : HF_FP64_ONLY));
         if (rc != HF_OK) return rc;
         t_fock += now_s() - tf;
         E = E_el + S->E_nn;
         if (energies) energies[it - 1] = E;
+        if (mixed) res->mixed_iterations++;
         // DIIS error e = FPS - SPF = T - T^T with T = F P S
         S_K(gemm(N, N, N, 1.0, Fslot, N, false, P.as<double>(), N, false, 0.0, T1.as<double>(), N, st));
         S_K(gemm(N, N, N, 1.0, T1.as<double>(), N, false, S->S.as<double>(), N, false, 0.0, T2.as<double>(), N, st));
@@ -282,9 +287,13 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
         HF_CUDA(cudaStreamSynchronize(st));
         res->last_dE = it > 1 ? fabs(E - E_old) : INFINITY;
         res->last_dP = dP;
-        if (it > 1 && fabs(E - E_old) < o.e_tol && dP < o.d_tol) {
+        if (!mixed && it > 1 && fabs(E - E_old) < o.e_tol && dP < o.d_tol) {
             converged = 1;
             break;
+        }
+        if (mixed && it > 1 && fabs(E - E_old) < o.mixed_switch) {
+            mixed = false;  // switch to FP64-only builds; the mixed-phase Fock matrices leave the DIIS history
+            nh = 0;
         }
         E_old = E;
         std::swap(P.p, Pn.p);

@@ -78,7 +78,8 @@ class SystemInfo_c(ctypes.Structure):
 
 class ScfOpts_c(ctypes.Structure):
     _fields_ = [("n_occ", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("e_tol", ctypes.c_double),
-                ("d_tol", ctypes.c_double), ("diis_size", ctypes.c_int32), ("diis_off", ctypes.c_int32)]
+                ("d_tol", ctypes.c_double), ("diis_size", ctypes.c_int32), ("diis_off", ctypes.c_int32),
+                ("mixed_switch", ctypes.c_double)]
 
 
 class ScfResult_c(ctypes.Structure):
@@ -86,7 +87,7 @@ class ScfResult_c(ctypes.Structure):
                 ("converged", ctypes.c_int32), ("last_dE", ctypes.c_double), ("last_dP", ctypes.c_double),
                 ("seconds_total", ctypes.c_double), ("seconds_fock", ctypes.c_double),
                 ("seconds_diag", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int32), ("n_kept", ctypes.c_int32),
-                ("s_min", ctypes.c_double)]
+                ("s_min", ctypes.c_double), ("mixed_iterations", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class BatchInfo_c(ctypes.Structure):
@@ -356,10 +357,11 @@ class Batch:
 
 
 def scf(system: "System", n_occ: int = 0, max_iter: int = 100, e_tol: float = 1e-9, d_tol: float = 1e-6,
-        diis_size: int = 8, P_guess=None, raise_on_noconv: bool = True) -> dict:
+        diis_size: int = 8, P_guess=None, raise_on_noconv: bool = True, mixed_switch: float = 1e-5) -> dict:
     """hf_scf_run with host arrays; returns energy, density, orbital energies and timings."""
     N = system.n_bf
-    o = ScfOpts_c(int(n_occ), int(max_iter), float(e_tol), float(d_tol), int(diis_size), 1 if diis_size == 0 else 0)
+    o = ScfOpts_c(int(n_occ), int(max_iter), float(e_tol), float(d_tol), int(diis_size), 1 if diis_size == 0 else 0,
+                  float(mixed_switch))
     P_out = np.empty((N, N))
     eps = np.zeros(N)
     en = np.zeros(max_iter)
