@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--prim-tau", type=float, default=1e-14)
-    ap.add_argument("--mode", default="fock", choices=["fock", "scf", "mixed", "batch"])
+    ap.add_argument("--mode", default="fock", choices=["fock", "scf", "mixed", "batch", "guess"])
+    ap.add_argument("--n-train", type=int, default=2000)
+    ap.add_argument("--n-eval", type=int, default=32)
+    ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--n-mol", type=int, default=512)
     a = ap.parse_args()
     if a.mode == "mixed" and "--waters" not in sys.argv:
@@ -440,6 +443,35 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+def run_guess(a):
+    """Learned initial guess: train on plain-SCF densities of U{2..8}-water clusters (seeds (5,m)), then
+    compare SCF iterations/time from the learned vs the core-Hamiltonian guess on 32-water clusters (seeds (6,m))."""
+    import numpy as np
+    from paper_1708_00033_gb300 import guess, hf
+    ctx = hf.Context(0)
+    logs = []
+    log = lambda s: (logs.append(s), print(s, file=sys.stderr, flush=True))  # noqa: E731
+    data = guess.make_dataset(ctx, a.n_train, log=log)
+    model = hf.Model(ctx, guess.init_weights(0))
+    t0 = time.perf_counter()
+    losses = guess.train(model, data, steps=a.train_steps, batch=2048, lr=1e-3, log=log)
+    train_s = time.perf_counter() - t0
+    np.save(os.path.join(tempfile.gettempdir(), "hf_guess_weights.npy"), model.weights())
+    ev = guess.evaluate(ctx, model, n_eval=a.n_eval, waters=32, log=log)
+    line = {"metric": "SCF time to converged energy, learned vs core-Hamiltonian guess", "value": ev["mean_learned_s"],
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": a.n_eval, "warmup": 0, "dtype": "bf16+f32 (MLP), f64 (SCF)",
+            "data": "synthetic",
+            "config": {"workload": f"train {a.n_train} clusters U{{2..8}} waters seeds (5,m); eval {a.n_eval} 32-water clusters seeds (6,m)",
+                       "schwarz_tau": 1e-10, "prim_tau": 1e-14, "train_steps": a.train_steps},
+            "dataset_s": data["seconds"], "train_samples": int(data["X"].shape[0]), "train_s": train_s,
+            "final_loss": float(np.mean(losses[-100:])), "initial_loss": float(np.mean(losses[:10])),
+            "mean_core_iterations": ev["mean_core_iterations"], "mean_learned_iterations": ev["mean_learned_iterations"],
+            "mean_core_s": ev["mean_core_s"], "mean_learned_s": ev["mean_learned_s"],
+            "speedup": ev["mean_core_s"] / ev["mean_learned_s"], "max_abs_dE": ev["max_abs_dE"],
+            "fallbacks": ev["fallbacks"], "rows": ev["rows"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -450,6 +482,8 @@ def main():
         run_mixed(a)
     elif a.mode == "batch":
         run_batch(a)
+    elif a.mode == "guess":
+        run_guess(a)
     else:
         run_ours(a)
 

@@ -301,6 +301,65 @@ int hf_fock_build_batch(hf_batch* batch, const double* P, double* F, double* E_e
  * HF_E_CUDA. */
 int hf_batch_tune(hf_batch* batch, const char* cache_path, int64_t sample_quartets);
 
+/* --------------------------------------------------------- learned guess */
+
+/* A small MLP that predicts density-matrix blocks from atom-pair geometry, as
+ * an SCF starting point.  The paper has no counterpart (its SCF starts from
+ * the core Hamiltonian, Section 3); the plain SCF is the fallback and the
+ * judge of the result, so a guess changes iteration counts, never the
+ * converged energy.
+ *   features (16 per unordered atom pair a <= b): R, u = (r_b - r_a)/R (3),
+ *     u_i u_j (9), one-hot element pair (O-O, O-H, H-H); for O-H the O atom
+ *     is first; on-site pairs have R = 0 and u = 0.
+ *   network: 16 -> 256 -> 256 -> 325, SiLU after the first two layers; the
+ *     325 outputs are three heads: O-O 15x15 (0..224), O-H 15x5 (225..299),
+ *     H-H 5x5 (300..324), row-major, rows = first atom's functions.
+ *   weights (float, in this order): W1[256][16], b1[256], W2[256][256],
+ *     b2[256], W3[325][256], b3[325]; BF16 copies are used in the products,
+ *     FP32 master copies in Adam, activations and accumulation are FP32.
+ * Supported atoms: O with 15 and H with 5 contiguous Cartesian functions. */
+#define HF_GUESS_FEATURES 16
+#define HF_GUESS_WIDTH 256
+#define HF_GUESS_OUTPUTS 325
+
+typedef struct hf_model hf_model;
+
+/* Number of floats in the weight vector (158,277). */
+int64_t hf_model_num_params(void);
+
+/* Create a model from host weights (hf_model_num_params floats). */
+int hf_model_create(hf_ctx* ctx, const float* init_weights, hf_model** model);
+void hf_model_destroy(hf_model* model);
+
+/* Copy the FP32 master weights and/or the last gradients to host arrays
+ * (either may be NULL). */
+int hf_model_get_weights(hf_model* model, float* weights, float* gradients);
+
+/* Y[n][325] = MLP(X[n][16]).  flags: HF_PTR_DEVICE for device X, Y. */
+int hf_model_forward(hf_model* model, int n, const float* X, float* Y, int flags);
+
+/* One training step on a minibatch (device pointers, HF_PTR_DEVICE
+ * required): loss = (1/n) sum_i sum_j mask_ij (Y_ij - T_ij)^2, gradients by
+ * backpropagation, then one Adam step (beta 0.9/0.999, eps 1e-8) with
+ * learning rate lr (lr = 0 computes the gradients only).  *loss (host) may be
+ * NULL. */
+int hf_model_train_step(hf_model* model, int n, const float* X, const float* T, const float* mask, float lr,
+                        float* loss, int flags);
+
+/* Features of every unordered atom pair of a system.  *n_pairs =
+ * n_atoms (n_atoms + 1) / 2; with X and meta NULL only the count is
+ * returned.  X[n_pairs][16]; meta[n_pairs][4] = (first function of the row
+ * atom, first function of the column atom, head 0/1/2, on-site flag).
+ * flags: HF_PTR_DEVICE for device X/meta.  Errors: HF_E_UNSUPPORTED for
+ * atoms other than the supported O and H. */
+int hf_guess_features(hf_system* sys, float* X, int32_t* meta, int64_t* n_pairs, int flags);
+
+/* Predicted total density P[N*N]: MLP blocks placed at (a, b) and (b, a),
+ * on-site blocks symmetrised, scaled so that tr(PS) = N_e.  flags:
+ * HF_PTR_DEVICE.  Errors: HF_E_INVALID if the prediction is not finite or
+ * tr(PS) <= 0 (the caller then falls back to the core guess). */
+int hf_guess_predict(hf_model* model, hf_system* sys, double* P, int flags);
+
 /* ------------------------------------------------- allocation-free build */
 
 /* Largest system (basis functions) hf_fock_build_noalloc accepts. */

@@ -216,6 +216,21 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
         Zd[a] = geom->Z[a];
         nel += geom->Z[a];
     }
+    S->Z_h.assign(geom->Z, geom->Z + na);
+    S->atom_bf0_h.assign(na, -1);
+    S->atom_nbf_h.assign(na, 0);
+    {
+        int last = -1;
+        for (int s = 0; s < ns; s++) {
+            const int a = basis->atom[s];
+            if (S->atom_bf0_h[a] < 0) S->atom_bf0_h[a] = bf0[s];
+            else if (last != a) S->atom_nbf_h[a] = -1000000;  // shells of this atom are not contiguous
+            S->atom_nbf_h[a] += (basis->l[s] + 1) * (basis->l[s] + 2) / 2;
+            last = a;
+        }
+        for (int a = 0; a < na; a++)
+            if (S->atom_nbf_h[a] < 0) S->atom_bf0_h[a] = -1;
+    }
     S->n_atoms = na;
     S->n_shells = ns;
     S->n_bf = nbf;

@@ -166,4 +166,7 @@ struct hf_system {
     hf::DevBuf class_q[hf::kNumPairClasses];  // sorted bounds of class_ids
     hf::DevBuf Qall, counts, staging_P, staging_out, bad, Bprim, prim_count;
     int maxpp = 0;
+    // host copies used by the learned guess: nuclear charges, first basis
+    // function and function count of each atom (-1 if its shells are not contiguous)
+    std::vector<int> Z_h, atom_bf0_h, atom_nbf_h;
 };

@@ -147,6 +147,17 @@ def load_library():
     lib.hf_fock_build_batch.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float),
                                         ctypes.c_int]
     lib.hf_batch_tune.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
+    lib.hf_model_num_params.restype = ctypes.c_int64
+    lib.hf_model_num_params.argtypes = []
+    lib.hf_model_create.argtypes = [vp, vp, ctypes.POINTER(vp)]
+    lib.hf_model_destroy.argtypes = [vp]
+    lib.hf_model_destroy.restype = None
+    lib.hf_model_get_weights.argtypes = [vp, vp, vp]
+    lib.hf_model_forward.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
+    lib.hf_model_train_step.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.c_int]
+    lib.hf_guess_features.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+    lib.hf_guess_predict.argtypes = [vp, vp, vp, ctypes.c_int]
     _lib = lib
     return lib
 
@@ -354,6 +365,84 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Model:
+    """hf_model_create: the learned-guess MLP (weights live on the device)."""
+
+    N_FEAT, WIDTH, N_OUT = 16, 256, 325
+
+    def __init__(self, ctx: Context, weights: np.ndarray):
+        self.ctx = ctx
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        if w.size != num_params():
+            raise ValueError("weight vector has the wrong length")
+        self._h = ctypes.c_void_p()
+        _check(load_library().hf_model_create(ctx._h, w.ctypes.data, ctypes.byref(self._h)), "hf_model_create")
+
+    def weights(self, gradients: bool = False) -> np.ndarray:
+        out = np.empty(num_params(), dtype=np.float32)
+        if gradients:
+            _check(load_library().hf_model_get_weights(self._h, None, out.ctypes.data), "hf_model_get_weights")
+        else:
+            _check(load_library().hf_model_get_weights(self._h, out.ctypes.data, None), "hf_model_get_weights")
+        return out
+
+    def forward(self, X):
+        """X [n, 16]: numpy (host path) or CUDA float32 tensor (device path)."""
+        if hasattr(X, "is_cuda") and X.is_cuda:
+            torch = _torch()
+            Y = torch.empty((X.shape[0], self.N_OUT), dtype=torch.float32, device=X.device)
+            _check(load_library().hf_model_forward(self._h, int(X.shape[0]), X.data_ptr(), Y.data_ptr(),
+                                                   HF_PTR_DEVICE), "hf_model_forward")
+            return Y
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.empty((X.shape[0], self.N_OUT), dtype=np.float32)
+        _check(load_library().hf_model_forward(self._h, int(X.shape[0]), X.ctypes.data, Y.ctypes.data, HF_PTR_HOST),
+               "hf_model_forward")
+        return Y
+
+    def train_step(self, X, T, mask, lr: float) -> float:
+        """One Adam step on CUDA float32 tensors; returns the minibatch loss."""
+        loss = ctypes.c_float(0.0)
+        _check(load_library().hf_model_train_step(self._h, int(X.shape[0]), X.data_ptr(), T.data_ptr(),
+                                                  mask.data_ptr(), float(lr), ctypes.byref(loss), HF_PTR_DEVICE),
+               "hf_model_train_step")
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().hf_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def num_params() -> int:
+    return int(load_library().hf_model_num_params())
+
+
+def guess_features(system: "System"):
+    """Host arrays X [n_pairs, 16] float32 and meta [n_pairs, 4] int32."""
+    n = ctypes.c_int64(0)
+    _check(load_library().hf_guess_features(system._h, None, None, ctypes.byref(n), 0), "hf_guess_features")
+    X = np.empty((n.value, 16), dtype=np.float32)
+    meta = np.empty((n.value, 4), dtype=np.int32)
+    _check(load_library().hf_guess_features(system._h, X.ctypes.data, meta.ctypes.data, ctypes.byref(n), HF_PTR_HOST),
+           "hf_guess_features")
+    return X, meta
+
+
+def guess_predict(model: Model, system: "System") -> np.ndarray:
+    P = np.empty((system.n_bf, system.n_bf))
+    _check(load_library().hf_guess_predict(model._h, system._h, P.ctypes.data, HF_PTR_HOST), "hf_guess_predict")
+    return P
 
 
 def scf(system: "System", n_occ: int = 0, max_iter: int = 100, e_tol: float = 1e-9, d_tol: float = 1e-6,
