@@ -294,8 +294,9 @@ int hf_batch_offsets(const hf_batch* batch, int64_t* off);
 int hf_fock_build_batch(hf_batch* batch, const double* P, double* F, double* E_elec, float* ms, int flags);
 
 /* Autotuner: for every class kernel, time each candidate (block size 64/128/
- * 256, chunk 32/128/512 quartets, 2/4/8 blocks per SM) on the first
- * sample_quartets quartets (0: 2e6) and keep the fastest; choices are read
+ * 256, chunk 32/128/512 quartets, 2/4/8 blocks per SM) on the class's first
+ * quartets - as many as take about 2e10 algorithmic operations, at most
+ * sample_quartets (0: 2e6) - and keep the fastest; choices are read
  * from and written to cache_path (one "class block chunk blocks_per_sm" line
  * per class) when it is not NULL.  Re-captures the graph.  Errors: HF_E_INVALID,
  * HF_E_CUDA. */

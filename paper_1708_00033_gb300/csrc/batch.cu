@@ -401,9 +401,12 @@ int hf_batch_tune(hf_batch* B, const char* cache_path, int64_t sample_quartets)
     const int blocks[] = {64, 128, 256};
     const int chunks[] = {32, 128, 512};
     const int bpss[] = {2, 4, 8};
-    const long long limit = sample_quartets > 0 ? sample_quartets : 2000000;
     for (int c = 0; c < kNumClasses; c++) {
         if (have[c] || B->n_total[c] <= 0) continue;
+        // sample about 2e10 algorithmic operations per candidate launch (a few ms), at most sample_quartets
+        const double per_quartet = 81.0 * kEriClasses[c].prim_flops + kEriClasses[c].cont_flops;
+        long long limit = (long long)(2e10 / per_quartet);
+        limit = std::max(2048LL, std::min(limit, sample_quartets > 0 ? (long long)sample_quartets : 2000000LL));
         float best = 1e30f;
         int best_bl = B->block[c], best_ch = B->chunk[c], best_bp = B->bps[c];
         for (int bl : blocks)

@@ -148,8 +148,8 @@ int hf_create(hf_ctx** out, int device, void* cuda_stream)
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     c->num_sms = prop.multiProcessorCount;
-    int rc = c->boys64.alloc(sizeof(double) * kBoysRows * kBoysCols);
-    if (rc == HF_OK) rc = c->boys32.alloc(sizeof(float) * kBoysRows * kBoysCols);
+    int rc = c->boys64.alloc(sizeof(double) * kBoysRows * kBoysStride64);
+    if (rc == HF_OK) rc = c->boys32.alloc(sizeof(float) * kBoysRows * kBoysStride32);
     if (rc == HF_OK && build_boys_tables(c->boys64.as<double>(), c->boys32.as<float>(), c->stream) != 0)
         rc = cuda_status(cudaGetLastError(), "boys table kernel");
     if (rc == HF_OK) {

@@ -22,41 +22,53 @@ struct PrimPair {
     real PAx, PAy, PAz;  // P - A
     real K;              // c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p
     real oo2p;           // 1 / (2p)
-    real B;              // primitive-pair Schwarz bound sqrt(max |[ab|ab]|), normalised components
+    float B;             // primitive-pair Schwarz bound sqrt(max |[ab|ab]|), normalised components
 };
 
-// Boys table: rows T_k = k / 32 for k = 0..kBoysRows-1 (T < 60); columns
-// F_0..F_14 at T_k and exp(-T_k) in the last column.
+// Boys tables, rows T_k = k / 32 for k = 0..kBoysRows-1 (T < 60), stored in
+// Taylor-coefficient form so that evaluation is a pure Horner chain:
+//   FP64 row: c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..6) at m*7 + j,
+//             e^{-T_k} / j! (j = 0..7) at 63 + j;
+//   FP32 row: c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..3) at m*4 + j,
+//             e^{-T_k} / j! (j = 0..4) at 36 + j.
 constexpr int kBoysRows = 1921;
-constexpr int kBoysCols = 16;
-constexpr int kBoysExpCol = 15;
+constexpr int kBoysStride64 = 72;
+constexpr int kBoysStride32 = 44;
+constexpr int kBoysExp64 = 63;
+constexpr int kBoysExp32 = 36;
 constexpr double kBoysTmax = 60.0;
 
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
-// F_m(T), m = 0..L.  Below T = 60: seven-term Taylor expansion about the
-// nearest grid point (|T - T_k| <= 1/64, truncation < 5e-17 relative), using
-// dF_m/dT = -F_{m+1}; for L >= 2 only F_L is expanded and the rest follow by
-// the downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1), with exp(-T)
-// itself expanded about T_k.  Above: F_0 = sqrt(pi/T)/2 and the upward
-// recursion F_{m+1} = (2m+1) F_m / (2T) (exp(-T) < 1e-26 is dropped).
+// F_m(T), m = 0..L.  Below T = 60: Taylor expansion about the nearest grid
+// point T_k (|T - T_k| <= 1/64; seven terms, truncation < 5e-17 relative),
+// using dF_m/dT = -F_{m+1}; for L >= 2 only F_L is expanded and the rest
+// follow from the downward recursion F_m = (2T F_{m+1} + e^{-T}) / (2m+1),
+// with e^{-T} = e^{-T_k} e^{T_k - T} expanded the same way.  Above: F_0 =
+// sqrt(pi/T)/2 and the upward recursion F_{m+1} = (2m+1) F_m / (2T)
+// (e^{-T} < 1e-26 is dropped).  The grid index is the integer that
+// T*32 + 1.5*2^52 rounds to, read from the low word of the sum.
 template <int L>
 __device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double* F)
 {
     if (T < kBoysTmax) {
-        const int k = __double2int_rn(T * 32.0);
-        const double d = k * (1.0 / 32.0) - T;
-        const double* __restrict__ r = tab + k * kBoysCols;
-        const double d2 = d * 0.5, d3 = d * (1.0 / 3.0), d4 = d * 0.25, d5 = d * 0.2, d6 = d * (1.0 / 6.0);
+        const double big = 6755399441055744.0;  // 1.5 * 2^52
+        const double t = fma(T, 32.0, big);
+        const int k = __double2loint(t);
+        const double d = fma(t - big, 1.0 / 32.0, -T);  // T_k - T
+        const double* __restrict__ r = tab + k * kBoysStride64;
         if constexpr (L <= 1) {
 #pragma unroll
-            for (int m = 0; m <= L; m++)
-                F[m] = r[m] + d * (r[m + 1] + d2 * (r[m + 2] + d3 * (r[m + 3] + d4 * (r[m + 4] + d5 * (r[m + 5] + d6 * r[m + 6])))));
+            for (int m = 0; m <= L; m++) {
+                const double* c = r + 7 * m;
+                F[m] = c[0] + d * (c[1] + d * (c[2] + d * (c[3] + d * (c[4] + d * (c[5] + d * c[6])))));
+            }
         } else {
-            F[L] = r[L] + d * (r[L + 1] + d2 * (r[L + 2] + d3 * (r[L + 3] + d4 * (r[L + 4] + d5 * (r[L + 5] + d6 * r[L + 6])))));
-            const double d7 = d * (1.0 / 7.0);
-            const double e = r[kBoysExpCol] * (1.0 + d * (1.0 + d2 * (1.0 + d3 * (1.0 + d4 * (1.0 + d5 * (1.0 + d6 * (1.0 + d7)))))));
+            const double* c = r + 7 * L;
+            F[L] = c[0] + d * (c[1] + d * (c[2] + d * (c[3] + d * (c[4] + d * (c[5] + d * c[6])))));
+            const double* x = r + kBoysExp64;
+            const double e = x[0] + d * (x[1] + d * (x[2] + d * (x[3] + d * (x[4] + d * (x[5] + d * (x[6] + d * x[7]))))));
             const double t2 = T + T;
 #pragma unroll
             for (int m = L - 1; m >= 0; m--) F[m] = (t2 * F[m + 1] + e) * (1.0 / (2 * m + 1));
@@ -78,16 +90,22 @@ template <int L>
 __device__ __forceinline__ void boys_eval(float T, const float* __restrict__ tab, float* F)
 {
     if (T < (float)kBoysTmax) {
-        const int k = __float2int_rn(T * 32.0f);
-        const float d = k * (1.0f / 32.0f) - T;
-        const float* __restrict__ r = tab + k * kBoysCols;
-        const float d2 = d * 0.5f, d3 = d * (1.0f / 3.0f);
+        const float big = 12582912.0f;  // 1.5 * 2^23
+        const float t = fmaf(T, 32.0f, big);
+        const int k = __float_as_int(t) - 0x4B400000;
+        const float d = fmaf(t - big, 1.0f / 32.0f, -T);
+        const float* __restrict__ r = tab + k * kBoysStride32;
         if constexpr (L <= 1) {
 #pragma unroll
-            for (int m = 0; m <= L; m++) F[m] = r[m] + d * (r[m + 1] + d2 * (r[m + 2] + d3 * r[m + 3]));
+            for (int m = 0; m <= L; m++) {
+                const float* c = r + 4 * m;
+                F[m] = c[0] + d * (c[1] + d * (c[2] + d * c[3]));
+            }
         } else {
-            F[L] = r[L] + d * (r[L + 1] + d2 * (r[L + 2] + d3 * r[L + 3]));
-            const float e = r[kBoysExpCol] * (1.0f + d * (1.0f + d2 * (1.0f + d3 * (1.0f + d * 0.25f))));
+            const float* c = r + 4 * L;
+            F[L] = c[0] + d * (c[1] + d * (c[2] + d * c[3]));
+            const float* x = r + kBoysExp32;
+            const float e = x[0] + d * (x[1] + d * (x[2] + d * (x[3] + d * x[4])));
             const float t2 = T + T;
 #pragma unroll
             for (int m = L - 1; m >= 0; m--) F[m] = (t2 * F[m + 1] + e) * (1.0f / (2 * m + 1));
@@ -139,7 +157,7 @@ constexpr int kEriThreads = 128;
         const real* P = (const real*)(sizeof(real) == 8 ? (const void*)a.P64 : (const void*)a.P32);                                  \
         const real* bt = (const real*)(sizeof(real) == 8 ? (const void*)a.boys64 : (const void*)a.boys32);  \
         const long long stride = (long long)gridDim.x * blockDim.x;                                          \
-        const real ptau = (real)a.prim_tau;                                                                  \
+        const float ptau = (float)a.prim_tau;                                                                \
         unsigned nprimq = 0;                                                                                 \
         for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_quartets; q += stride) { \
             const int b = find_bra(a.offsets, a.n_bra, q);                                                   \
@@ -175,14 +193,14 @@ constexpr int kEriThreads = 128;
         const PairHdr h = a.pairs[pid];                                                                      \
         const PrimPair<double>* pr = (const PrimPair<double>*)a.prims64;                                     \
         double qm = 0.0;                                                                                     \
-        quartet_##NAME<double>(h, h, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm, 0.0);             \
+        quartet_##NAME<double>(h, h, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm, 0.0f);             \
         a.Q[pid] = sqrt(qm);                                                                                 \
         for (int k = 0; k < h.nprim; k++) { /* bound of each primitive pair alone */                         \
             PairHdr h1 = h;                                                                                  \
             h1.prim0 = h.prim0 + k;                                                                          \
             h1.nprim = 1;                                                                                    \
             double qk = 0.0;                                                                                 \
-            quartet_##NAME<double>(h1, h1, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qk, 0.0);       \
+            quartet_##NAME<double>(h1, h1, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qk, 0.0f);       \
             a.Bprim[h.prim0 + k] = sqrt(qk);                                                                 \
         }                                                                                                    \
     }                                                                                                        \
@@ -199,7 +217,7 @@ constexpr int kEriThreads = 128;
     __global__ void __launch_bounds__(256) k_eri_batch_##NAME(const BatchArgs a)                            \
     {                                                                                                        \
         const int lane = threadIdx.x & 31;                                                                   \
-        const double ptau = a.prim_tau;                                                                      \
+        const float ptau = (float)a.prim_tau;                                                                \
         for (;;) {                                                                                           \
             unsigned long long base = 0;                                                                     \
             if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);                        \

@@ -379,10 +379,10 @@ def gen_class(X, Y):
     out.append(f"__device__ __forceinline__ int quartet_{name}(const PairHdr& hb, const PairHdr& hk,"
                f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
     out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
-    out.append(f"    real ptau)")
+    out.append(f"    float ptau)")
     out.append("{")
     out.append("    int nq = 0;")
-    out.append("    const real kB0 = prims[hk.prim0].B;")
+    out.append("    const float kB0 = prims[hk.prim0].B;")
     for l in acc_decl:
         out.append("    " + l)
     out.append("    for (int ib = 0; ib < hb.nprim; ib++) {")

@@ -128,21 +128,34 @@ __device__ __forceinline__ void jacobi_cs(const double* __restrict__ A, int n, i
     s = t * c;
 }
 
+// Rotations of one round: pair k -> (p, q, c, s), from the matrix at the start of the round.
+struct Rot {
+    int p, q;
+    double c, s;
+};
+
+__global__ void k_jacobi_rot(int n, int r, const double* __restrict__ A, Rot* __restrict__ rot)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n / 2) return;
+    Rot o;
+    rr_pair(n, r, k, o.p, o.q);
+    jacobi_cs(A, n, o.p, o.q, o.c, o.s);
+    rot[k] = o;
+}
+
 // One round: thread (kr, kc) transforms the 2x2 block of rows (p_r, q_r) and
 // columns (p_c, q_c) of A into Anew, and the entries (p_r|q_r, p_c|q_c) of V.
-__global__ void k_jacobi_round(int n, int r, const double* __restrict__ A, double* __restrict__ Anew,
-                               double* __restrict__ V)
+__global__ void k_jacobi_round(int n, const Rot* __restrict__ rot, const double* __restrict__ A,
+                               double* __restrict__ Anew, double* __restrict__ V)
 {
     const int half = n / 2;
     const int kc = blockIdx.x * blockDim.x + threadIdx.x;
     const int kr = blockIdx.y;
     if (kc >= half || kr >= half) return;
-    int pr, qr, pc, qc;
-    rr_pair(n, r, kr, pr, qr);
-    rr_pair(n, r, kc, pc, qc);
-    double cr, sr, cc, sc;
-    jacobi_cs(A, n, pr, qr, cr, sr);
-    jacobi_cs(A, n, pc, qc, cc, sc);
+    const Rot R = rot[kr], C = rot[kc];
+    const int pr = R.p, qr = R.q, pc = C.p, qc = C.q;
+    const double cr = R.c, sr = R.s, cc = C.c, sc = C.s;
     const double a = A[(size_t)pr * n + pc], b = A[(size_t)pr * n + qc];
     const double c = A[(size_t)qr * n + pc], d = A[(size_t)qr * n + qc];
     // columns: A J_c
@@ -279,6 +292,7 @@ int jacobi_eigh(int n, const double* Ain, double* w, double* Vout, int ncols, do
     double* part = V + (size_t)m * m;
     double* res = part + 512;
     double* key = res + 2;
+    Rot* rot = (Rot*)key;  // m/2 rotations (12 m bytes) in the key area, which the final sort reuses
     // padding eigenvalue: far above the spectrum bound (Gershgorin of |A| <= n max|A|) is not known here;
     // a zero-coupled padding entry only needs to be distinct and is dropped from the output.
     k_jacobi_init<<<(unsigned)(((long long)m * m + 255) / 256), 256, 0, s>>>(n, m, Ain, A0, V, 0.0);
@@ -293,10 +307,10 @@ int jacobi_eigh(int n, const double* Ain, double* w, double* Vout, int ncols, do
         if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
         if (h[0] <= tol * tol * h[1] || h[0] == 0.0) break;
         for (int r = 0; r < m - 1; r++) {
-            // off-diagonal blocks of Anew not touched by this round do not exist: every entry
-            // belongs to exactly one (row pair, column pair) block.
+            // every entry of Anew belongs to exactly one (row pair, column pair) block of this round
+            k_jacobi_rot<<<(m / 2 + 127) / 128, 128, 0, s>>>(m, r, cur, rot);
             dim3 grid((m / 2 + 127) / 128, m / 2);
-            k_jacobi_round<<<grid, 128, 0, s>>>(m, r, cur, nxt, V);
+            k_jacobi_round<<<grid, 128, 0, s>>>(m, rot, cur, nxt, V);
             double* t = cur;
             cur = nxt;
             nxt = t;
@@ -512,7 +526,7 @@ size_t jacobi_work_doubles(int n)
     const size_t m = (size_t)(n + (n & 1));
     size_t mp = 1;
     while (mp < m) mp <<= 1;
-    return 3 * m * m + 514 + mp;
+    return 3 * m * m + 514 + mp + 2 * m;
 }
 size_t jacobi_work_ints(int n)
 {

@@ -198,8 +198,15 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
         Xp = Us.as<double>() + drop;
         ldx = N;
     }
+    DevBuf Vprev, Vj, Fw;
+    S_TRY(Vprev.alloc(NN * sizeof(double)));
+    S_TRY(Vj.alloc(NN * sizeof(double)));
+    S_TRY(Fw.alloc(NN * sizeof(double)));
+    bool have_prev = false;
     auto diagonalise = [&](const double* Fm, double* Pout, double* eps) -> int {
-        // F' = X^T F X (nx x nx), eigenpairs, C_occ = X C'_occ, P = 2 C_occ C_occ^T
+        // F' = X^T F X (nx x nx), eigenpairs, C_occ = X C'_occ, P = 2 C_occ C_occ^T.  After the
+        // first iteration F' is rotated into the previous eigenvectors' basis, where it is nearly
+        // diagonal, so the Jacobi sweeps start close to convergence (V = V_prev V_jacobi).
         double tt = now_s();
         if (gemm(N, nx, N, 1.0, Fm, N, false, Xp, ldx, false, 0.0, T1.as<double>(), nx, st)) return -1;
         if (gemm(nx, nx, N, 1.0, Xp, ldx, true, T1.as<double>(), nx, false, 0.0, Fp.as<double>(), nx, st)) return -1;
@@ -211,8 +218,25 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
             if (rc != HF_OK) return rc;
             e = &e2;
         }
-        rc = e->run(Fp.as<double>(), eps, Vp.as<double>(), nx, &sweeps, st);
-        if (rc != HF_OK) return rc;
+        if (have_prev) {
+            if (gemm(nx, nx, nx, 1.0, Fp.as<double>(), nx, false, Vprev.as<double>(), nx, false, 0.0, T1.as<double>(),
+                     nx, st))
+                return -1;
+            if (gemm(nx, nx, nx, 1.0, Vprev.as<double>(), nx, true, T1.as<double>(), nx, false, 0.0, Fw.as<double>(),
+                     nx, st))
+                return -1;
+            rc = e->run(Fw.as<double>(), eps, Vj.as<double>(), nx, &sweeps, st);
+            if (rc != HF_OK) return rc;
+            if (gemm(nx, nx, nx, 1.0, Vprev.as<double>(), nx, false, Vj.as<double>(), nx, false, 0.0, Vp.as<double>(),
+                     nx, st))
+                return -1;
+        } else {
+            rc = e->run(Fp.as<double>(), eps, Vp.as<double>(), nx, &sweeps, st);
+            if (rc != HF_OK) return rc;
+        }
+        if (cudaMemcpyAsync(Vprev.p, Vp.p, (size_t)nx * nx * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return -1;
+        have_prev = true;
         // C_occ = X[:, :nx] * V[:, :n_occ]  (V is nx x nx, row-major, first n_occ columns)
         if (gemm(N, n_occ, nx, 1.0, Xp, ldx, false, Vp.as<double>(), nx, false, 0.0, Cocc.as<double>(), n_occ, st))
             return -1;

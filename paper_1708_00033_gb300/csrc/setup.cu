@@ -14,13 +14,14 @@ namespace hf {
 // F_m(T_k), m = 0..14, at T_k = k/32: the series
 //   F_M(T) = exp(-T) sum_i (2T)^i / ((2M+1)(2M+3)...(2M+2i+1))
 // for the top order (compensated summation of its positive terms), then the
-// downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).
+// downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1); stored as the
+// Taylor coefficients F_{m+j}(T_k) / j! and exp(-T_k) / j! (see eri_common.cuh).
 __global__ void k_boys_table(double* t64, float* t32)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= kBoysRows) return;
     const double T = k / 32.0;
-    const int M = kBoysCols - 2;
+    const int M = 14;
     double term = 1.0 / (2 * M + 1), sum = term, comp = 0.0;
     for (int i = 1; i < 1000; i++) {
         term *= 2.0 * T / (2 * M + 2 * i + 1);
@@ -31,15 +32,23 @@ __global__ void k_boys_table(double* t64, float* t32)
         if (term < 1e-21 * sum) break;
     }
     const double e = exp(-T);
-    double F[kBoysCols - 1];
+    double F[M + 1];
     F[M] = e * sum;
     for (int m = M - 1; m >= 0; m--) F[m] = (2.0 * T * F[m + 1] + e) / (2 * m + 1);
-    for (int m = 0; m <= M; m++) {
-        t64[k * kBoysCols + m] = F[m];
-        t32[k * kBoysCols + m] = (float)F[m];
+    double* r = t64 + (size_t)k * kBoysStride64;
+    float* q = t32 + (size_t)k * kBoysStride32;
+    for (int i = 0; i < kBoysStride64; i++) r[i] = 0.0;
+    for (int i = 0; i < kBoysStride32; i++) q[i] = 0.0f;
+    double fact = 1.0;
+    for (int j = 0; j <= 7; j++) {
+        if (j > 0) fact *= j;
+        for (int m = 0; m <= 8; m++) {
+            if (j <= 6) r[7 * m + j] = F[m + j] / fact;
+            if (j <= 3) q[4 * m + j] = (float)(F[m + j] / fact);
+        }
+        r[kBoysExp64 + j] = e / fact;
+        if (j <= 4) q[kBoysExp32 + j] = (float)(e / fact);
     }
-    t64[k * kBoysCols + kBoysExpCol] = e;
-    t32[k * kBoysCols + kBoysExpCol] = (float)e;
 }
 
 int build_boys_tables(double* t64, float* t32, cudaStream_t s)
@@ -149,7 +158,7 @@ __global__ void k_build_pairs(long long n_pairs, int maxpp, const int* __restric
             r.PAz = r.Pz - Az;
             r.K = ca * cb * exp(-a * b * ip * R2) * c52 * ip;
             r.oo2p = 0.5 * ip;
-            r.B = 0.0;  // set by the Schwarz pass; 0 never stops a primitive loop whose threshold is 0
+            r.B = 0.0f;  // set by the Schwarz pass; 0 never stops a primitive loop whose threshold is 0
             p64[t * maxpp + k] = r;
             PrimPair<float> f;
             f.p = (float)r.p;
@@ -265,7 +274,7 @@ __global__ void k_sort_prims(long long n_pairs, const PairHdr* __restrict__ pair
     if (t >= n_pairs) return;
     const int o = pairs[t].prim0, n = pairs[t].nprim;
     for (int k = 0; k < n; k++) {
-        p64[o + k].B = Bprim[o + k];
+        p64[o + k].B = (float)Bprim[o + k];
         p32[o + k].B = (float)Bprim[o + k];
     }
     for (int i = 1; i < n; i++) {  // insertion sort, descending B
