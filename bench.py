@@ -458,7 +458,7 @@ def run_guess(a):
     train_s = time.perf_counter() - t0
     np.save(os.path.join(tempfile.gettempdir(), "hf_guess_weights.npy"), model.weights())
     ev = guess.evaluate(ctx, model, n_eval=a.n_eval, waters=32, log=log)
-    line = {"metric": "SCF time to converged energy, learned vs core-Hamiltonian guess", "value": ev["mean_learned_s"],
+    line = {"metric": "SCF time to converged energy, learned vs core-Hamiltonian guess", "value": ev["mean_mixed_learned_s"],
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": a.n_eval, "warmup": 0, "dtype": "bf16+f32 (MLP), f64 (SCF)",
             "data": "synthetic",
             "config": {"workload": f"train {a.n_train} clusters U{{2..8}} waters seeds (5,m); eval {a.n_eval} 32-water clusters seeds (6,m)",
@@ -466,8 +466,12 @@ def run_guess(a):
             "dataset_s": data["seconds"], "train_samples": int(data["X"].shape[0]), "train_s": train_s,
             "final_loss": float(np.mean(losses[-100:])), "initial_loss": float(np.mean(losses[:10])),
             "mean_core_iterations": ev["mean_core_iterations"], "mean_learned_iterations": ev["mean_learned_iterations"],
+            "mean_mixed_learned_iterations": ev["mean_mixed_learned_iterations"],
             "mean_core_s": ev["mean_core_s"], "mean_learned_s": ev["mean_learned_s"],
-            "speedup": ev["mean_core_s"] / ev["mean_learned_s"], "max_abs_dE": ev["max_abs_dE"],
+            "mean_mixed_learned_s": ev["mean_mixed_learned_s"],
+            "speedup_learned": ev["mean_core_s"] / ev["mean_learned_s"],
+            "speedup_mixed_learned": ev["mean_core_s"] / ev["mean_mixed_learned_s"],
+            "max_abs_dE": ev["max_abs_dE"], "max_abs_dE_mixed": ev["max_abs_dE_mixed"],
             "fallbacks": ev["fallbacks"], "rows": ev["rows"]}
     print(json.dumps(line), flush=True)
 

@@ -31,6 +31,7 @@ int cuda_status(cudaError_t e, const char* what)
 int DevBuf::alloc(size_t n)
 {
     release();
+    owned = true;
     if (n == 0) n = 16;
     cudaError_t e = cudaMalloc(&p, n);
     if (e != cudaSuccess) {
@@ -45,9 +46,10 @@ int DevBuf::alloc(size_t n)
 
 void DevBuf::release()
 {
-    if (p) cudaFree(p);
+    if (p && owned) cudaFree(p);
     p = nullptr;
     bytes = 0;
+    owned = true;
 }
 
 namespace {
@@ -157,6 +159,17 @@ int hf_create(hf_ctx** out, int device, void* cuda_stream)
         if (e != cudaSuccess) rc = cuda_status(e, "hf_create sync");
     }
     if (rc == HF_OK) {
+        // Reserve per-thread local memory for the largest ERI kernel once, so that launches of the
+        // spilling high-angular-momentum kernels do not grow and shrink the reservation each time.
+        size_t need = 0;
+        for (int ci = 0; ci < kNumClasses; ci++) need = std::max(need, kEriClasses[ci].local_bytes());
+        size_t cur = 0;
+        if (cudaDeviceGetLimit(&cur, cudaLimitStackSize) == cudaSuccess && need > cur)
+            if (cudaDeviceSetLimit(cudaLimitStackSize, need) != cudaSuccess)
+                rc = cuda_status(cudaGetLastError(), "hf_create: local memory reservation");
+        cudaGetLastError();
+    }
+    if (rc == HF_OK) {
         for (auto& ev : c->ev) {
             if (cudaEventCreate(&ev) != cudaSuccess) {
                 rc = cuda_status(cudaGetLastError(), "cudaEventCreate");
@@ -193,6 +206,27 @@ void hf_destroy(hf_ctx* c)
 }
 
 }  // extern "C"
+
+// Carves 256-byte-aligned views out of one allocation.
+struct Arena {
+    size_t used = 0;
+    std::vector<std::pair<DevBuf*, size_t>> items;
+    void add(DevBuf& b, size_t bytes)
+    {
+        items.push_back({&b, used});
+        b.bytes = bytes;
+        used += (bytes + 255) & ~(size_t)255;
+    }
+    int commit(DevBuf& owner)
+    {
+        TRY(owner.alloc(used ? used : 256));
+        for (auto& it : items) {
+            const size_t n = it.first->bytes;
+            it.first->view((char*)owner.p + it.second, n);
+        }
+        return HF_OK;
+    }
+};
 
 static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* basis)
 {
@@ -236,111 +270,139 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
     S->n_bf = nbf;
     S->n_electrons = nel;
     X.maxpp = maxnp * maxnp;
-    TRY(upload(S->sh_l, basis->l, ns, st));
-    TRY(upload(S->sh_atom, basis->atom, ns, st));
-    TRY(upload(S->sh_bf0, bf0.data(), ns, st));
-    TRY(upload(S->sh_nprim, basis->nprim, ns, st));
-    TRY(upload(S->sh_prim0, prim0.data(), ns, st));
-    TRY(upload(S->sh_exp, basis->exps, npr, st));
+    const long long npairs = (long long)ns * (ns + 1) / 2;
+    if (npairs * (long long)X.maxpp >= (1ll << 31)) return fail(HF_E_UNSUPPORTED, "too many primitive pairs");
+    S->n_pairs_all = (int)npairs;
+    const size_t NN = (size_t)nbf * nbf;
+
+    // ---------------------------------------------- inputs, matrices, pairs
     DevBuf coef_in;
-    TRY(upload(coef_in, basis->coefs, npr, st));
-    TRY(upload(S->atom_xyz, geom->xyz, 3 * (size_t)na, st));
-    TRY(upload(S->atom_Z, Zd.data(), na, st));
-    TRY(S->sh_coef.alloc(sizeof(double) * npr));
-    TRY(S->comp_norm.alloc(sizeof(double) * nbf));
+    Arena a1;
+    a1.add(S->sh_l, sizeof(int) * ns);
+    a1.add(S->sh_atom, sizeof(int) * ns);
+    a1.add(S->sh_bf0, sizeof(int) * ns);
+    a1.add(S->sh_nprim, sizeof(int) * ns);
+    a1.add(S->sh_prim0, sizeof(int) * ns);
+    a1.add(S->sh_exp, sizeof(double) * npr);
+    a1.add(coef_in, sizeof(double) * npr);
+    a1.add(S->atom_xyz, sizeof(double) * 3 * na);
+    a1.add(S->atom_Z, sizeof(double) * na);
+    a1.add(S->sh_coef, sizeof(double) * npr);
+    a1.add(S->comp_norm, sizeof(double) * nbf);
+    a1.add(S->Ebuf, sizeof(double) * 320);
+    a1.add(S->pairs, sizeof(PairHdr) * npairs);
+    a1.add(S->prims64, sizeof(PrimPair<double>) * npairs * X.maxpp);
+    a1.add(S->prims32, sizeof(PrimPair<float>) * npairs * X.maxpp);
+    a1.add(S->pair_class, sizeof(int) * npairs);
+    a1.add(X.counts, sizeof(unsigned long long) * 16);
+    a1.add(X.Qall, sizeof(double) * npairs);
+    a1.add(X.Bprim, sizeof(double) * npairs * X.maxpp);
+    TRY(a1.commit(X.arena_in));
+    Arena a2;
+    a2.add(S->S, NN * sizeof(double));
+    a2.add(S->H, NN * sizeof(double));
+    a2.add(S->P64, NN * sizeof(double));
+    if (S->th.fp32_cutoff > 0.0) a2.add(S->P32, NN * sizeof(float));
+    a2.add(S->Jt, NN * sizeof(double));
+    a2.add(S->Kt, NN * sizeof(double));
+    a2.add(S->F, NN * sizeof(double));
+    a2.add(X.staging_P, NN * sizeof(double));
+    a2.add(X.staging_out, 2 * NN * sizeof(double));
+    a2.add(X.bad, sizeof(int));
+    a2.add(X.prim_count, sizeof(unsigned long long) * 2 * kNumClasses);
+    TRY(a2.commit(X.arena_mat));
+    HF_CUDA(cudaMemcpyAsync(S->sh_l.p, basis->l, sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(S->sh_atom.p, basis->atom, sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(S->sh_bf0.p, bf0.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(S->sh_nprim.p, basis->nprim, sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(S->sh_prim0.p, prim0.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(S->sh_exp.p, basis->exps, sizeof(double) * npr, cudaMemcpyHostToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(coef_in.p, basis->coefs, sizeof(double) * npr, cudaMemcpyHostToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(S->atom_xyz.p, geom->xyz, sizeof(double) * 3 * na, cudaMemcpyHostToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(S->atom_Z.p, Zd.data(), sizeof(double) * na, cudaMemcpyHostToDevice, st));
     KCHK(launch_shell_coef(ns, S->sh_l.as<int>(), S->sh_nprim.as<int>(), S->sh_prim0.as<int>(), S->sh_exp.as<double>(),
                            coef_in.as<double>(), S->sh_coef.as<double>(), st));
     KCHK(launch_comp_norm(ns, S->sh_l.as<int>(), S->sh_bf0.as<int>(), S->comp_norm.as<double>(), st));
-    const size_t NN = (size_t)nbf * nbf;
-    TRY(S->S.alloc(NN * sizeof(double)));
-    TRY(S->H.alloc(NN * sizeof(double)));
     KCHK(launch_one_electron(ns, na, nbf, S->sh_l.as<int>(), S->sh_atom.as<int>(), S->sh_bf0.as<int>(),
                              S->sh_nprim.as<int>(), S->sh_prim0.as<int>(), S->sh_exp.as<double>(),
                              S->sh_coef.as<double>(), S->atom_xyz.as<double>(), S->atom_Z.as<double>(),
                              S->comp_norm.as<double>(), ctx->boys64.as<double>(), S->S.as<double>(),
                              S->H.as<double>(), st));
-    TRY(S->Ebuf.alloc(sizeof(double) * 320));
     KCHK(launch_nuclear_repulsion(na, S->atom_xyz.as<double>(), S->atom_Z.as<double>(), S->Ebuf.as<double>() + 300,
                                   st));
-    HF_CUDA(cudaMemcpyAsync(&S->E_nn, S->Ebuf.as<double>() + 300, sizeof(double), cudaMemcpyDeviceToHost, st));
-
-    // ---------------------------------------------------------- shell pairs
-    const long long npairs = (long long)ns * (ns + 1) / 2;
-    if (npairs * (long long)X.maxpp >= (1ll << 31)) return fail(HF_E_UNSUPPORTED, "too many primitive pairs");
-    S->n_pairs_all = (int)npairs;
-    TRY(S->pairs.alloc(sizeof(PairHdr) * npairs));
-    TRY(S->prims64.alloc(sizeof(PrimPair<double>) * npairs * X.maxpp));
-    TRY(S->prims32.alloc(sizeof(PrimPair<float>) * npairs * X.maxpp));
-    TRY(S->pair_class.alloc(sizeof(int) * npairs));
     KCHK(launch_build_pairs(npairs, X.maxpp, S->sh_l.as<int>(), S->sh_atom.as<int>(), S->sh_bf0.as<int>(),
                             S->sh_nprim.as<int>(), S->sh_prim0.as<int>(), S->sh_exp.as<double>(),
                             S->sh_coef.as<double>(), S->atom_xyz.as<double>(), S->pairs.as<PairHdr>(),
                             S->prims64.p, S->prims32.p, S->pair_class.as<int>(), st));
-    TRY(X.counts.alloc(sizeof(unsigned long long) * 16));
-    HF_CUDA(cudaMemsetAsync(X.counts.p, 0, sizeof(unsigned long long) * 16, st));
-    KCHK(launch_class_count(npairs, S->pair_class.as<int>(), X.counts.as<unsigned long long>(), st));
+    unsigned long long* cnt_dev = X.counts.as<unsigned long long>();  // [0..5] class counts, [8..15] cursors
+    HF_CUDA(cudaMemsetAsync(cnt_dev, 0, sizeof(unsigned long long) * 16, st));
+    KCHK(launch_class_count(npairs, S->pair_class.as<int>(), cnt_dev, st));
     unsigned long long cnt_all[kNumPairClasses];
-    HF_CUDA(cudaMemcpyAsync(cnt_all, X.counts.p, sizeof(cnt_all), cudaMemcpyDeviceToHost, st));
-    HF_CUDA(cudaStreamSynchronize(st));
+    HF_CUDA(cudaMemcpyAsync(cnt_all, cnt_dev, sizeof(cnt_all), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));  // host sync 1 of 2: class sizes
 
-    // ------------------------------------------------------ Schwarz bounds
-    TRY(X.Qall.alloc(sizeof(double) * npairs));
+    // ------------------------------------------------------ schedule arena
+    size_t npad[kNumPairClasses], seg[kNumPairClasses + 1], base_all[kNumPairClasses + 1];
+    seg[0] = base_all[0] = 0;
+    for (int c = 0; c < kNumPairClasses; c++) {
+        npad[c] = cnt_all[c] ? next_pow2(cnt_all[c]) : 0;
+        seg[c + 1] = seg[c] + npad[c];
+        base_all[c + 1] = base_all[c] + cnt_all[c];
+    }
+    DevBuf ids_all, key, val, rb;
+    DevBuf c64[kNumClasses], c32[kNumClasses];
+    Arena a3;
+    a3.add(ids_all, sizeof(int) * (npairs ? npairs : 1));
+    a3.add(key, sizeof(double) * (seg[kNumPairClasses] ? seg[kNumPairClasses] : 1));
+    a3.add(val, sizeof(int) * (seg[kNumPairClasses] ? seg[kNumPairClasses] : 1));
+    a3.add(rb, 512);  // readback block: unsigned nsig[8] | long long totals[2*21] | double E_nn
+    for (int ci = 0; ci < kNumClasses; ci++) {
+        const size_t cap = cnt_all[kEriClasses[ci].X];
+        auto& pl = S->plan[ci];
+        a3.add(c64[ci], sizeof(long long) * (cap ? cap : 1));
+        a3.add(c32[ci], sizeof(long long) * (cap ? cap : 1));
+        a3.add(pl.kstart32, sizeof(int) * (cap ? cap : 1));
+        a3.add(pl.offsets64, sizeof(long long) * (cap + 1));
+        a3.add(pl.offsets32, sizeof(long long) * (cap + 1));
+    }
+    TRY(a3.commit(X.arena_sched));
+    unsigned* nsig_dev = rb.as<unsigned>();
+    long long* totals_dev = (long long*)(rb.as<char>() + 32);
+    double* enn_dev = (double*)(rb.as<char>() + 32 + 8 * 2 * kNumClasses);
+    HF_CUDA(cudaMemsetAsync(rb.p, 0, 512, st));
+
+    // --------------------------------------------------- Schwarz bounds
     HF_CUDA(cudaMemsetAsync(X.Qall.p, 0, sizeof(double) * npairs, st));
-    TRY(X.Bprim.alloc(sizeof(double) * npairs * X.maxpp));
     HF_CUDA(cudaMemsetAsync(X.Bprim.p, 0, sizeof(double) * npairs * X.maxpp, st));
-    std::vector<DevBuf> ids_all(kNumPairClasses);
     for (int c = 0; c < kNumPairClasses; c++) {
         if (!cnt_all[c]) continue;
-        TRY(ids_all[c].alloc(sizeof(int) * cnt_all[c]));
-        HF_CUDA(cudaMemsetAsync(X.counts.as<unsigned long long>() + 8, 0, sizeof(unsigned long long), st));
-        KCHK(launch_class_scatter_all(npairs, S->pair_class.as<int>(), c,
-                                      (unsigned*)(X.counts.as<unsigned long long>() + 8), ids_all[c].as<int>(), st));
-        const int ci = class_index(c, c);
+        int* ids = ids_all.as<int>() + base_all[c];
+        KCHK(launch_class_scatter_all(npairs, S->pair_class.as<int>(), c, (unsigned*)(cnt_dev + 8 + c), ids, st));
         SchwarzArgs sa;
         sa.pairs = S->pairs.as<PairHdr>();
         sa.prims64 = S->prims64.p;
-        sa.ids = ids_all[c].as<int>();
+        sa.ids = ids;
         sa.n = (int)cnt_all[c];
         sa.Q = X.Qall.as<double>();
         sa.boys64 = ctx->boys64.as<double>();
         sa.Bprim = X.Bprim.as<double>();
-        kEriClasses[ci].launch_schwarz(sa, kEriThreads, st);
+        kEriClasses[class_index(c, c)].launch_schwarz(sa, kEriThreads, st);
         HF_CUDA(cudaGetLastError());
     }
     KCHK(launch_sort_prims(npairs, S->pairs.as<PairHdr>(), X.Bprim.as<double>(), S->prims64.p, S->prims32.p, st));
-    HF_CUDA(cudaMemsetAsync(X.counts.as<unsigned long long>() + 9, 0, sizeof(unsigned long long), st));
-    KCHK(launch_copy_q(npairs, X.Qall.as<double>(), S->pairs.as<PairHdr>(), X.counts.as<unsigned long long>() + 9, st));
-    unsigned long long qbits = 0;
-    HF_CUDA(cudaMemcpyAsync(&qbits, X.counts.as<unsigned long long>() + 9, sizeof(qbits), cudaMemcpyDeviceToHost, st));
-    HF_CUDA(cudaStreamSynchronize(st));
-    memcpy(&S->Qmax, &qbits, sizeof(double));
+    unsigned long long* qbits_dev = cnt_dev + 7;
+    HF_CUDA(cudaMemsetAsync(qbits_dev, 0, sizeof(unsigned long long), st));
+    KCHK(launch_copy_q(npairs, X.Qall.as<double>(), S->pairs.as<PairHdr>(), qbits_dev, st));
 
     // ------------------------------------- significant pairs, sorted by Q
     const double tau = S->th.schwarz_tau;
+    KCHK(launch_sig_scatter(npairs, (long long)seg[kNumPairClasses], S->pair_class.as<int>(), X.Qall.as<double>(),
+                            qbits_dev, tau, seg, nsig_dev, key.as<double>(), val.as<int>(), st));
     for (int c = 0; c < kNumPairClasses; c++) {
-        S->class_count[c] = 0;
-        if (!cnt_all[c]) continue;
-        const size_t npad = next_pow2(cnt_all[c]);
-        DevBuf key, val;
-        TRY(key.alloc(sizeof(double) * npad));
-        TRY(val.alloc(sizeof(int) * npad));
-        HF_CUDA(cudaMemsetAsync(X.counts.as<unsigned long long>() + 10, 0, sizeof(unsigned long long), st));
-        KCHK(launch_class_scatter_sig(npairs, S->pair_class.as<int>(), X.Qall.as<double>(), c, S->Qmax, tau,
-                                      (unsigned*)(X.counts.as<unsigned long long>() + 10), key.as<double>(),
-                                      val.as<int>(), st));
-        unsigned nsig = 0;
-        HF_CUDA(cudaMemcpyAsync(&nsig, X.counts.as<unsigned long long>() + 10, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                st));
-        HF_CUDA(cudaStreamSynchronize(st));
-        S->class_count[c] = (int)nsig;
-        if (!nsig) continue;
-        const size_t npad2 = next_pow2(nsig);
-        KCHK(bitonic_sort_desc(key.as<double>(), val.as<int>(), (int)nsig, (int)npad2, st));
-        TRY(S->class_ids[c].alloc(sizeof(int) * nsig));
-        TRY(X.class_q[c].alloc(sizeof(double) * nsig));
-        HF_CUDA(cudaMemcpyAsync(S->class_ids[c].p, val.p, sizeof(int) * nsig, cudaMemcpyDeviceToDevice, st));
-        HF_CUDA(cudaMemcpyAsync(X.class_q[c].p, key.p, sizeof(double) * nsig, cudaMemcpyDeviceToDevice, st));
-        HF_CUDA(cudaStreamSynchronize(st));
+        if (!npad[c]) continue;
+        KCHK(bitonic_sort_desc(key.as<double>() + seg[c], val.as<int>() + seg[c], (int)npad[c], (int)npad[c], st));
+        S->class_ids[c].view(val.as<int>() + seg[c], sizeof(int) * npad[c]);
+        X.class_q[c].view(key.as<double>() + seg[c], sizeof(double) * npad[c]);
     }
 
     // ------------------------------------------------- quartet schedule
@@ -351,37 +413,32 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
         pl.n_unscreened = (Xc == Yc) ? (long long)cnt_all[Xc] * (cnt_all[Xc] + 1) / 2
                                      : (long long)cnt_all[Xc] * (long long)cnt_all[Yc];
         S->quartets_total += pl.n_unscreened;
-        pl.n64 = pl.n32 = 0;
-        const int nb = S->class_count[Xc], nk = S->class_count[Yc];
-        if (!nb || !nk) continue;
-        DevBuf c64, c32;
-        TRY(c64.alloc(sizeof(long long) * nb));
-        TRY(c32.alloc(sizeof(long long) * nb));
-        TRY(pl.kstart32.alloc(sizeof(int) * nb));
-        TRY(pl.offsets64.alloc(sizeof(long long) * (nb + 1)));
-        TRY(pl.offsets32.alloc(sizeof(long long) * (nb + 1)));
-        KCHK(launch_ket_counts(nb, X.class_q[Xc].as<double>(), nk, X.class_q[Yc].as<double>(), Xc == Yc, tau,
-                               S->th.fp32_cutoff, c64.as<long long>(), c32.as<long long>(), pl.kstart32.as<int>(), st));
-        KCHK(launch_scan(nb, c64.as<long long>(), pl.offsets64.as<long long>(), st));
-        KCHK(launch_scan(nb, c32.as<long long>(), pl.offsets32.as<long long>(), st));
-        HF_CUDA(cudaMemcpyAsync(&pl.n64, pl.offsets64.as<long long>() + nb, sizeof(long long), cudaMemcpyDeviceToHost,
-                                st));
-        HF_CUDA(cudaMemcpyAsync(&pl.n32, pl.offsets32.as<long long>() + nb, sizeof(long long), cudaMemcpyDeviceToHost,
-                                st));
-        HF_CUDA(cudaStreamSynchronize(st));
+        const int cap = (int)cnt_all[Xc];
+        if (!cap || !cnt_all[Yc]) continue;
+        KCHK(launch_ket_counts_dev(cap, nsig_dev + Xc, X.class_q[Xc].as<double>(), nsig_dev + Yc,
+                                   X.class_q[Yc].as<double>(), Xc == Yc, tau, S->th.fp32_cutoff, c64[ci].as<long long>(),
+                                   c32[ci].as<long long>(), pl.kstart32.as<int>(), st));
+        KCHK(launch_scan(cap, c64[ci].as<long long>(), pl.offsets64.as<long long>(), st));
+        KCHK(launch_scan(cap, c32[ci].as<long long>(), pl.offsets32.as<long long>(), st));
+        HF_CUDA(cudaMemcpyAsync(totals_dev + 2 * ci, pl.offsets64.as<long long>() + cap, sizeof(long long),
+                                cudaMemcpyDeviceToDevice, st));
+        HF_CUDA(cudaMemcpyAsync(totals_dev + 2 * ci + 1, pl.offsets32.as<long long>() + cap, sizeof(long long),
+                                cudaMemcpyDeviceToDevice, st));
     }
-
-    // ------------------------------------------------------- work buffers
-    TRY(S->P64.alloc(NN * sizeof(double)));
-    if (S->th.fp32_cutoff > 0.0) TRY(S->P32.alloc(NN * sizeof(float)));
-    TRY(S->Jt.alloc(NN * sizeof(double)));
-    TRY(S->Kt.alloc(NN * sizeof(double)));
-    TRY(S->F.alloc(NN * sizeof(double)));
-    TRY(X.staging_P.alloc(NN * sizeof(double)));
-    TRY(X.staging_out.alloc(2 * NN * sizeof(double)));
-    TRY(X.bad.alloc(sizeof(int)));
-    TRY(X.prim_count.alloc(sizeof(unsigned long long) * 2 * kNumClasses));
-    HF_CUDA(cudaStreamSynchronize(st));
+    HF_CUDA(cudaMemcpyAsync(enn_dev, S->Ebuf.as<double>() + 300, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    HF_CUDA(cudaMemcpyAsync(enn_dev + 1, qbits_dev, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    unsigned char rbh[512];
+    HF_CUDA(cudaMemcpyAsync(rbh, rb.p, 512, cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));  // host sync 2 of 2: significant counts, quartet totals, E_nn
+    const unsigned* nsig_h = (const unsigned*)rbh;
+    const long long* totals_h = (const long long*)(rbh + 32);
+    memcpy(&S->E_nn, rbh + 32 + 8 * 2 * kNumClasses, sizeof(double));
+    memcpy(&S->Qmax, rbh + 32 + 8 * 2 * kNumClasses + 8, sizeof(double));
+    for (int c = 0; c < kNumPairClasses; c++) S->class_count[c] = (int)nsig_h[c];
+    for (int ci = 0; ci < kNumClasses; ci++) {
+        S->plan[ci].n64 = totals_h[2 * ci];
+        S->plan[ci].n32 = totals_h[2 * ci + 1];
+    }
     HF_CUDA(cudaGetLastError());
     return HF_OK;
 }
@@ -556,10 +613,13 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
                 a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
                 a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
                 a.n_quartets = n;
-                const long long blocks = (n + kEriThreads - 1) / kEriThreads;
-                const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
                 const int use_f32 = prec && !(flags & HF_FP64_ONLY);
-                kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st);
+                // a class too small to fill the GPU with one thread per quartet shares each quartet's
+                // primitive work among a lane group instead (shorter latency, same result)
+                const int lanes = (!use_f32 && n < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
+                const long long blocks = (n * lanes + kEriThreads - 1) / kEriThreads;
+                const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
+                kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st, lanes);
                 HF_CUDA(cudaGetLastError());
             }
             if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * ci + 2 * prec + 1], st));

@@ -149,38 +149,66 @@ constexpr int kEriThreads = 128;
 
 // Kernels and host launchers of one class.  The digestion weight of a unique
 // shell quartet is f = 1/((1+d_AB)(1+d_CD)(1+d_AB,CD)).
-#define ERI_CLASS_KERNELS(NAME, X, Y)                                                                        \
-    template <typename real>                                                                                 \
+#define ERI_CLASS_KERNELS(NAME, X, Y, GL)                                                                    \
+    template <typename real, int GK>                                                                         \
     __global__ void __launch_bounds__(kEriThreads) k_eri_##NAME(const EriArgs a)                            \
     {                                                                                                        \
         const PrimPair<real>* prims = (const PrimPair<real>*)(sizeof(real) == 8 ? a.prims64 : a.prims32);   \
-        const real* P = (const real*)(sizeof(real) == 8 ? (const void*)a.P64 : (const void*)a.P32);                                  \
+        const real* P = (const real*)(sizeof(real) == 8 ? (const void*)a.P64 : (const void*)a.P32);          \
         const real* bt = (const real*)(sizeof(real) == 8 ? (const void*)a.boys64 : (const void*)a.boys32);  \
-        const long long stride = (long long)gridDim.x * blockDim.x;                                          \
         const float ptau = (float)a.prim_tau;                                                                \
         unsigned nprimq = 0;                                                                                 \
-        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_quartets; q += stride) { \
-            const int b = find_bra(a.offsets, a.n_bra, q);                                                   \
-            const int k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                            \
-            const PairHdr hb = a.pairs[a.bra[b]];                                                            \
-            const PairHdr hk = a.pairs[a.ket[k]];                                                            \
+        constexpr int gpw = 32 / GK;                                                                         \
+        const int lane = threadIdx.x & (GK - 1);                                                             \
+        const int grp = (threadIdx.x & 31) / GK;                                                             \
+        const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                      \
+        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;                                   \
+        for (long long wb = warp * gpw; wb < a.n_quartets; wb += nwarps * gpw) { /* warp-uniform */          \
+            const long long q = wb + grp;                                                                    \
+            const bool valid = q < a.n_quartets;                                                             \
+            PairHdr hb, hk;                                                                                  \
             double f = 1.0;                                                                                  \
-            if (hb.A == hb.B) f *= 0.5;                                                                      \
-            if (hk.A == hk.B) f *= 0.5;                                                                      \
-            if (a.same && b == k) f *= 0.5;                                                                  \
-            nprimq += quartet_##NAME<real>(hb, hk, prims, bt, P, a.N, f, a.Jt, a.Kt, nullptr, ptau);         \
+            if (valid) {                                                                                     \
+                const int b = find_bra(a.offsets, a.n_bra, q);                                               \
+                const int k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                        \
+                hb = a.pairs[a.bra[b]];                                                                      \
+                hk = a.pairs[a.ket[k]];                                                                      \
+                if (hb.A == hb.B) f *= 0.5;                                                                  \
+                if (hk.A == hk.B) f *= 0.5;                                                                  \
+                if (a.same && b == k) f *= 0.5;                                                              \
+            } else {                                                                                         \
+                hb = hk = a.pairs[a.bra[0]];                                                                 \
+            }                                                                                                \
+            nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, a.Jt, a.Kt, nullptr, ptau, lane,   \
+                                               valid);                                                       \
         }                                                                                                    \
         if (a.prim_count) {                                                                                  \
             const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \
             if ((threadIdx.x & 31) == 0 && w) atomicAdd(a.prim_count, w);                                    \
         }                                                                                                    \
     }                                                                                                        \
-    void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s)              \
+    void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s, int lanes)   \
     {                                                                                                        \
         if (use_f32)                                                                                         \
-            k_eri_##NAME<float><<<grid, block, 0, s>>>(a);                                                   \
+            k_eri_##NAME<float, 1><<<grid, block, 0, s>>>(a);                                                \
+        else if (lanes > 1)                                                                                  \
+            k_eri_##NAME<double, (GL)><<<grid, block, 0, s>>>(a);                                            \
         else                                                                                                 \
-            k_eri_##NAME<double><<<grid, block, 0, s>>>(a);                                                  \
+            k_eri_##NAME<double, 1><<<grid, block, 0, s>>>(a);                                               \
+    }                                                                                                        \
+    size_t local_bytes_##NAME()                                                                              \
+    {                                                                                                        \
+        cudaFuncAttributes fa;                                                                               \
+        size_t m = 0;                                                                                        \
+        if (cudaFuncGetAttributes(&fa, k_eri_##NAME<double, 1>) == cudaSuccess) m = fa.localSizeBytes;       \
+        if (cudaFuncGetAttributes(&fa, k_eri_##NAME<double, (GL)>) == cudaSuccess && fa.localSizeBytes > m)  \
+            m = fa.localSizeBytes;                                                                           \
+        if (cudaFuncGetAttributes(&fa, k_eri_##NAME<float, 1>) == cudaSuccess && fa.localSizeBytes > m)      \
+            m = fa.localSizeBytes;                                                                           \
+        if (cudaFuncGetAttributes(&fa, k_eri_batch_##NAME) == cudaSuccess && fa.localSizeBytes > m)          \
+            m = fa.localSizeBytes;                                                                           \
+        cudaGetLastError();                                                                                  \
+        return m;                                                                                            \
     }
 
 // Schwarz bounds of the pairs of a diagonal class: Q = sqrt(max |(ab|ab)|).
@@ -193,14 +221,14 @@ constexpr int kEriThreads = 128;
         const PairHdr h = a.pairs[pid];                                                                      \
         const PrimPair<double>* pr = (const PrimPair<double>*)a.prims64;                                     \
         double qm = 0.0;                                                                                     \
-        quartet_##NAME<double>(h, h, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm, 0.0f);             \
+        quartet_##NAME<double, 1>(h, h, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm, 0.0f, 0, true);             \
         a.Q[pid] = sqrt(qm);                                                                                 \
         for (int k = 0; k < h.nprim; k++) { /* bound of each primitive pair alone */                         \
             PairHdr h1 = h;                                                                                  \
             h1.prim0 = h.prim0 + k;                                                                          \
             h1.nprim = 1;                                                                                    \
             double qk = 0.0;                                                                                 \
-            quartet_##NAME<double>(h1, h1, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qk, 0.0f);       \
+            quartet_##NAME<double, 1>(h1, h1, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qk, 0.0f, 0, true);       \
             a.Bprim[h.prim0 + k] = sqrt(qk);                                                                 \
         }                                                                                                    \
     }                                                                                                        \
@@ -213,31 +241,42 @@ constexpr int kEriThreads = 128;
 // take chunks of the batch's quartet index space from a device counter (the
 // GPU analogue of the paper's dynamic load balancing, ddi_dlbnext); a quartet
 // index resolves to (molecule, bra, ket) by two binary searches.
-#define ERI_BATCH_KERNEL(NAME)                                                                               \
+#define ERI_BATCH_KERNEL(NAME, GL_UNUSED)                                                                           \
     __global__ void __launch_bounds__(256) k_eri_batch_##NAME(const BatchArgs a)                            \
     {                                                                                                        \
-        const int lane = threadIdx.x & 31;                                                                   \
+        const int wl = threadIdx.x & 31;                                                                     \
+        constexpr int GL = 1; /* batches have enough quartets per class for one thread per quartet */        \
+        const int lane = 0;                                                                                  \
+        const int grp = wl;                                                                                  \
+        constexpr int gpw = 32;                                                                              \
         const float ptau = (float)a.prim_tau;                                                                \
         for (;;) {                                                                                           \
             unsigned long long base = 0;                                                                     \
-            if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);                        \
+            if (wl == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);                          \
             base = __shfl_sync(0xffffffffu, base, 0);                                                        \
             if (base >= (unsigned long long)a.n_total) break;                                                \
             const long long end = min((long long)base + a.chunk, a.n_total);                                 \
-            for (long long q = (long long)base + lane; q < end; q += 32) {                                   \
-                const int m = find_bra(a.mol_off, a.n_mol, q);                                               \
+            for (long long wq = (long long)base; wq < end; wq += gpw) { /* warp-uniform */                  \
+                const long long q = wq + grp;                                                                \
+                const bool valid = q < end;                                                                  \
+                const int m = find_bra(a.mol_off, a.n_mol, valid ? q : (long long)base);                     \
                 const MolClass mc = a.mols[m];                                                               \
-                const long long ql = q - a.mol_off[m];                                                       \
-                const int b = find_bra(mc.offsets, mc.n_bra, ql);                                            \
-                const int k = (int)(ql - mc.offsets[b]);                                                     \
-                const PairHdr hb = mc.pairs[mc.bra[b]];                                                      \
-                const PairHdr hk = mc.pairs[mc.ket[k]];                                                      \
+                PairHdr hb, hk;                                                                              \
                 double f = 1.0;                                                                              \
-                if (hb.A == hb.B) f *= 0.5;                                                                  \
-                if (hk.A == hk.B) f *= 0.5;                                                                  \
-                if (mc.same && b == k) f *= 0.5;                                                             \
-                quartet_##NAME<double>(hb, hk, (const PrimPair<double>*)mc.prims64, a.boys64, mc.P64, mc.N, f, \
-                                       mc.Jt, mc.Kt, nullptr, ptau);                                         \
+                if (valid) {                                                                                 \
+                    const long long ql = q - a.mol_off[m];                                                   \
+                    const int b = find_bra(mc.offsets, mc.n_bra, ql);                                        \
+                    const int k = (int)(ql - mc.offsets[b]);                                                 \
+                    hb = mc.pairs[mc.bra[b]];                                                                \
+                    hk = mc.pairs[mc.ket[k]];                                                                \
+                    if (hb.A == hb.B) f *= 0.5;                                                              \
+                    if (hk.A == hk.B) f *= 0.5;                                                              \
+                    if (mc.same && b == k) f *= 0.5;                                                         \
+                } else {                                                                                     \
+                    hb = hk = mc.pairs[mc.bra[0]];                                                           \
+                }                                                                                            \
+                quartet_##NAME<double, (GL)>(hb, hk, (const PrimPair<double>*)mc.prims64, a.boys64, mc.P64, mc.N, f, \
+                                             mc.Jt, mc.Kt, nullptr, ptau, lane, valid);                      \
             }                                                                                                \
         }                                                                                                    \
     }                                                                                                        \

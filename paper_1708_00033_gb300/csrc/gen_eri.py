@@ -81,6 +81,9 @@ def first_nz(t):
 
 Z3 = (0, 0, 0)
 
+# lanes that share one shell quartet's primitive work, by total angular momentum
+LANES_BY_L = {0: 1, 1: 1, 2: 1, 3: 1, 4: 2, 5: 4, 6: 8, 7: 8, 8: 8}
+
 
 class Counter:
     def __init__(self):
@@ -375,35 +378,75 @@ def gen_class(X, Y):
     out.append(f"// ({PAIR_NAMES[X]}|{PAIR_NAMES[Y]}) class: l = {la}{lb}{lc}{ld}, "
                f"{len(targets)} [e0|f0] targets, {prim_flops} flops per primitive quartet, "
                f"{cnt.cont} per contracted quartet.")
-    out.append(f"template <typename real>")
+    G = LANES_BY_L[L]
+    out.append(f"// Lanes per quartet in the ERI kernels: {G}.  The G lanes of a group share one shell quartet's")
+    out.append(f"// primitive staircase round-robin and sum their accumulators with butterfly shuffles; lane 0")
+    out.append(f"// then runs the horizontal recurrence and the digestion.  Called warp-uniformly; a lane with")
+    out.append(f"// valid == false takes part in the shuffles only.")
+    out.append(f"template <typename real, int G>")
     out.append(f"__device__ __forceinline__ int quartet_{name}(const PairHdr& hb, const PairHdr& hk,"
                f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
     out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
-    out.append(f"    float ptau)")
+    out.append(f"    float ptau, int lane, bool valid)")
     out.append("{")
+    out.append("    // surviving primitive quartets form a staircase (pairs sorted by bound): bra primitive ib")
+    out.append("    // pairs with the first nk(ib) ket primitives, nk non-increasing; one flat loop over it")
+    out.append("    const PrimPair<real>* __restrict__ bpp = prims + hb.prim0;")
+    out.append("    const PrimPair<real>* __restrict__ kpp = prims + hk.prim0;")
+    out.append("    const int nbp = hb.nprim;")
+    out.append("    int nkb = hk.nprim;")
+    out.append("    int total = 0;")
+    out.append("    if (valid) {")
+    out.append("        for (int ib = 0, c = nkb; ib < nbp; ib++) {")
+    out.append("            const float Bb = bpp[ib].B;")
+    out.append("            while (c > 0 && Bb * kpp[c - 1].B < ptau) c--;")
+    out.append("            if (c == 0) break;")
+    out.append("            total += c;")
+    out.append("        }")
+    out.append("        while (nkb > 0 && bpp[0].B * kpp[nkb - 1].B < ptau) nkb--;")
+    out.append("    }")
     out.append("    int nq = 0;")
-    out.append("    const float kB0 = prims[hk.prim0].B;")
     for l in acc_decl:
         out.append("    " + l)
-    out.append("    for (int ib = 0; ib < hb.nprim; ib++) {")
-    out.append("        const PrimPair<real> bp = prims[hb.prim0 + ib];")
-    out.append("        if (bp.B * kB0 < ptau) break;  // primitive pairs are sorted by B, descending")
+    out.append("    // lane l evaluates staircase positions l, l + G, l + 2G, ... in lockstep with its group")
+    out.append("    int ib = 0, ik = 0;")
+    out.append("    auto advance = [&]() {")
+    out.append("        if (++ik == nkb) {")
+    out.append("            ik = 0;")
+    out.append("            ib++;")
+    out.append("            if (ib < nbp)")
+    out.append("                while (nkb > 0 && bpp[ib].B * kpp[nkb - 1].B < ptau) nkb--;")
+    out.append("        }")
+    out.append("    };")
+    out.append("    if (G > 1)")
+    out.append("        for (int s = 0; s < lane && s < total; s++) advance();")
+    out.append("    for (int it = (G > 1 ? lane : 0); it < total; it += G) {")
+    out.append("        const int cib = ib, cik = ik;")
+    out.append("#pragma unroll")
+    out.append("        for (int s = 0; s < G; s++) advance();")
+    out.append("        nq++;")
+    out.append("        const PrimPair<real> bp = bpp[cib];")
+    out.append("        const PrimPair<real> kp = kpp[cik];")
     out.append("        const real bK = bp.K, bo2p = bp.oo2p;")
     for a in AX:
         if f"PA{a}" in used:
             out.append(f"        const real PA{a} = bp.PA{a};")
-    out.append("        for (int ik = 0; ik < hk.nprim; ik++) {")
-    out.append("            const PrimPair<real> kp = prims[hk.prim0 + ik];")
-    out.append("            if (bp.B * kp.B < ptau) break;")
-    out.append("            nq++;")
     for l in setup:
-        out.append("            " + l)
+        out.append("        " + l)
     for l in vrr:
-        out.append("            " + l)
+        out.append("        " + l)
     for l in acc:
-        out.append("            " + l)
+        out.append("        " + l)
+    out.append("    }")
+    out.append("    if constexpr (G > 1) {")
+    out.append("#pragma unroll")
+    out.append("        for (int o = 1; o < G; o <<= 1) {")
+    for (e, f, m) in targets:
+        nm = f"acc{tstr(e)}_{tstr(f)}"
+        out.append(f"            {nm} += __shfl_xor_sync(0xffffffffu, {nm}, o);")
     out.append("        }")
     out.append("    }")
+    out.append("    if (!valid || lane != 0) return nq;")
     if need_ab:
         out.append("    const real ABx = (real)hb.ABx, ABy = (real)hb.ABy, ABz = (real)hb.ABz;")
     if need_cd:
@@ -417,6 +460,7 @@ def gen_class(X, Y):
         out.append("        *qout = qmax;")
     out.append("        return nq;")
     out.append("    }")
+    out.append("    if (total == 0) return nq;  // every primitive quartet screened: nothing to digest")
     out.append("    const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
     out.append("    const real fj = (real)(4.0 * fscale), fk = (real)(2.0 * fscale);")
     for l in dig:
@@ -424,11 +468,11 @@ def gen_class(X, Y):
     out.append("    return nq;")
     out.append("}")
     out.append("")
-    out.append(f"ERI_CLASS_KERNELS({name}, {X}, {Y})")
-    out.append(f"ERI_BATCH_KERNEL({name})")
+    out.append(f"ERI_BATCH_KERNEL({name}, {G})")
+    out.append(f"ERI_CLASS_KERNELS({name}, {X}, {Y}, {G})")
     if X == Y:
         out.append(f"SCHWARZ_KERNEL({name})")
-    info = dict(name=name, X=X, Y=Y, l=[la, lb, lc, ld], L=L, prim_flops=prim_flops, cont_flops=cnt.cont,
+    info = dict(name=name, X=X, Y=Y, l=[la, lb, lc, ld], L=L, G=G, prim_flops=prim_flops, cont_flops=cnt.cont,
                 hrr_flops=cont_hrr, targets=len(targets), vrr_nodes=len(vrr))
     return "\n".join(out) + "\n", info
 
@@ -456,17 +500,18 @@ def main(outdir):
     lines = ['// Generated by gen_eri.py: do not edit.', '#include "eri_common.cuh"', "", "namespace hf {"]
     for info in infos:
         n = info["name"]
-        lines.append(f"void launch_eri_{n}(const EriArgs&, int, int, int, cudaStream_t);")
+        lines.append(f"void launch_eri_{n}(const EriArgs&, int, int, int, cudaStream_t, int);")
         if info["X"] == info["Y"]:
             lines.append(f"void launch_schwarz_{n}(const SchwarzArgs&, int, cudaStream_t);")
         lines.append(f"void launch_eri_batch_{n}(const BatchArgs&, int, int, cudaStream_t);")
+        lines.append(f"size_t local_bytes_{n}();")
     lines.append("")
     lines.append("const EriClassEntry kEriClasses[kNumClasses] = {")
     for info in infos:
         n = info["name"]
         lines.append(f"    {{{info['X']}, {info['Y']}, {info['L']}, {info['prim_flops']}, {info['cont_flops']}, "
                      f"launch_eri_{n}, {('launch_schwarz_' + n) if info['X'] == info['Y'] else 'nullptr'}, \"{n}\", "
-                     f"launch_eri_batch_{n}}},")
+                     f"launch_eri_batch_{n}, local_bytes_{n}, {info['G']}}},")
     lines.append("};")
     lines.append("}  // namespace hf")
     text = "\n".join(lines) + "\n"

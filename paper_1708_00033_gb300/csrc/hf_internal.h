@@ -88,10 +88,12 @@ struct EriClassEntry {
     int X, Y, L;
     int prim_flops;  // per primitive quartet (setup + Boys + VRR + accumulation)
     int cont_flops;  // per contracted quartet (HRR + digestion)
-    void (*launch)(const EriArgs&, int use_f32, int grid, int block, cudaStream_t);
+    void (*launch)(const EriArgs&, int use_f32, int grid, int block, cudaStream_t, int lanes);
     void (*launch_schwarz)(const SchwarzArgs&, int block, cudaStream_t);
     const char* name;
     void (*launch_batch)(const BatchArgs&, int grid, int block, cudaStream_t);
+    size_t (*local_bytes)();  // largest per-thread local memory of the class's kernels
+    int lanes;                // lanes that share one shell quartet in the ERI kernels
 };
 extern const EriClassEntry kEriClasses[kNumClasses];
 
@@ -113,8 +115,17 @@ int cuda_status(cudaError_t e, const char* what);
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    bool owned = true;
     int alloc(size_t n);
     void release();
+    // non-owning view of part of another buffer (an arena)
+    void view(void* ptr, size_t n)
+    {
+        release();
+        p = ptr;
+        bytes = n;
+        owned = false;
+    }
     template <typename T>
     T* as() const { return (T*)p; }
     ~DevBuf() { release(); }
@@ -165,6 +176,7 @@ struct hf_system {
     // scratch
     hf::DevBuf class_q[hf::kNumPairClasses];  // sorted bounds of class_ids
     hf::DevBuf Qall, counts, staging_P, staging_out, bad, Bprim, prim_count;
+    hf::DevBuf arena_in, arena_mat, arena_sched;  // owners of the views above
     int maxpp = 0;
     // host copies used by the learned guess: nuclear charges, first basis
     // function and function count of each atom (-1 if its shells are not contiguous)

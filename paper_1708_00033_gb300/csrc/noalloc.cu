@@ -139,9 +139,10 @@ extern "C" int hf_fock_build_noalloc(hf_system* S, const double* P, double* F, d
             a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
             a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
             a.n_quartets = n;
-            const long long blocks = (n + kEriThreads - 1) / kEriThreads;
+            const int lanes = (!prec && n < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
+            const long long blocks = (n * lanes + kEriThreads - 1) / kEriThreads;
             const int grid = (int)(blocks < (long long)ctx->num_sms * 16 ? blocks : (long long)ctx->num_sms * 16);
-            kEriClasses[ci].launch(a, prec, grid, kEriThreads, st);
+            kEriClasses[ci].launch(a, prec, grid, kEriThreads, st, lanes);
             HF_CUDA(cudaGetLastError());
         }
     }

@@ -366,6 +366,107 @@ __global__ void k_scan(int n, const long long* __restrict__ in, long long* __res
     if (threadIdx.x == 0) out[n] = carry;
 }
 
+// --------------------------------------------- all-class scatter and counts --
+struct SegBase {
+    long long base[8];
+};
+
+__global__ void k_fill_keys(long long n, double* __restrict__ key, int* __restrict__ val)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        key[t] = -1.0;
+        val[t] = 0x7fffffff;
+    }
+}
+
+// significant pairs (Q * Qmax >= tau, or all when tau = 0) into their class segment
+__global__ void k_sig_scatter(long long n, const int* __restrict__ pclass, const double* __restrict__ Q,
+                              const unsigned long long* __restrict__ qmax_bits, double tau, SegBase seg,
+                              unsigned* __restrict__ cursor, double* __restrict__ key, int* __restrict__ val)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double q = Q[t];
+    if (tau > 0.0) {
+        const double qmax = __longlong_as_double((long long)*qmax_bits);
+        if (!(q * qmax >= tau)) return;
+    }
+    const int c = pclass[t];
+    const unsigned pos = atomicAdd(&cursor[c], 1u);
+    key[seg.base[c] + pos] = q;
+    val[seg.base[c] + pos] = (int)t;
+}
+
+int launch_sig_scatter(long long n_pairs, long long n_seg, const int* pclass, const double* Q,
+                       const unsigned long long* qmax_bits, double tau, const size_t* seg_host, unsigned* cursor,
+                       double* key, int* val, cudaStream_t s)
+{
+    SegBase sb;
+    for (int c = 0; c < 8; c++) sb.base[c] = c < 7 ? (long long)seg_host[c] : 0;
+    if (n_seg > 0) k_fill_keys<<<(unsigned)((n_seg + 255) / 256), 256, 0, s>>>(n_seg, key, val);
+    if (n_pairs > 0)
+        k_sig_scatter<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(n_pairs, pclass, Q, qmax_bits, tau, sb, cursor,
+                                                                       key, val);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// k_ket_counts with the list lengths read on the device (entries b >= n_bra get zero counts)
+__global__ void k_ket_counts_dev(int cap, const unsigned* __restrict__ n_bra_p, const double* __restrict__ qb,
+                                 const unsigned* __restrict__ n_ket_p, const double* __restrict__ qk, int same,
+                                 double tau, double cutoff, long long* __restrict__ c64, long long* __restrict__ c32,
+                                 int* __restrict__ kstart32)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= cap) return;
+    const int n_bra = (int)*n_bra_p, n_ket = (int)*n_ket_p;
+    if (b >= n_bra || n_ket == 0) {
+        c64[b] = 0;
+        c32[b] = 0;
+        kstart32[b] = 0;
+        return;
+    }
+    const double Qb = qb[b];
+    int n = n_ket;
+    if (tau > 0.0) {
+        int lo = 0, hi = n_ket;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (Qb * qk[mid] >= tau)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        n = lo;
+    }
+    if (same && n > b + 1) n = b + 1;
+    int n64 = n;
+    if (cutoff > 0.0) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (Qb * qk[mid] >= cutoff)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        n64 = lo;
+    }
+    c64[b] = n64;
+    c32[b] = n - n64;
+    kstart32[b] = n64;
+}
+
+int launch_ket_counts_dev(int cap, const unsigned* n_bra, const double* qb, const unsigned* n_ket, const double* qk,
+                          int same, double tau, double cutoff, long long* c64, long long* c32, int* kstart32,
+                          cudaStream_t s)
+{
+    if (cap > 0)
+        k_ket_counts_dev<<<(cap + 255) / 256, 256, 0, s>>>(cap, n_bra, qb, n_ket, qk, same, tau, cutoff, c64, c32,
+                                                            kstart32);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_shell_coef(int n_sh, const int* l, const int* nprim, const int* prim0, const double* exps,
                       const double* coefs, double* cn, cudaStream_t s)
 {

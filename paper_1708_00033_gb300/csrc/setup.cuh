@@ -23,6 +23,12 @@ int launch_sort_prims(long long n_pairs, const PairHdr* pairs, const double* Bpr
 int launch_ket_counts(int n_bra, const double* qb, int n_ket, const double* qk, int same, double tau, double cutoff,
                       long long* c64, long long* c32, int* kstart32, cudaStream_t s);
 int launch_scan(int n, const long long* in, long long* out, cudaStream_t s);
+int launch_sig_scatter(long long n_pairs, long long n_seg, const int* pclass, const double* Q,
+                       const unsigned long long* qmax_bits, double tau, const size_t* seg_host, unsigned* cursor,
+                       double* key, int* val, cudaStream_t s);
+int launch_ket_counts_dev(int cap, const unsigned* n_bra, const double* qb, const unsigned* n_ket, const double* qk,
+                          int same, double tau, double cutoff, long long* c64, long long* c32, int* kstart32,
+                          cudaStream_t s);
 
 // one-electron matrices (raw component normalisation; comp_norm applied inside)
 int launch_one_electron(int n_sh, int n_atoms, int N, const int* l, const int* atom, const int* bf0,

@@ -101,13 +101,20 @@ def predict_or_none(model: hf.Model, system: hf.System):
 
 
 def evaluate(ctx: hf.Context, model: hf.Model, n_eval: int = 32, waters: int = 32,
-             config: int = inputs.CONFIG_GUESS_EVAL, tau: float = 1e-10, prim_tau: float = 1e-14, log=None) -> dict:
+             config: int = inputs.CONFIG_GUESS_EVAL, tau: float = 1e-10, prim_tau: float = 1e-14,
+             fp32_cutoff: float = 1e-4, log=None) -> dict:
+    """Per held-out cluster, three SCFs to the same convergence test (|dE| < 1e-9, RMS dP < 1e-6):
+    plain FP64 from the core-Hamiltonian guess, FP64 from the learned guess, and mixed precision
+    (FP32 for Q_ij Q_kl < fp32_cutoff until |dE| < 1e-5, then FP64) from the learned guess.
+    SCF times exclude system setup, which is reported separately."""
     import torch
     rows = []
     for m in range(n_eval):
         geom = inputs.water_cluster(waters, config, m)
         basis = inputs.synthetic_basis(geom)
+        t0 = time.perf_counter()
         s = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=prim_tau)
+        setup64 = time.perf_counter() - t0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         core = hf.scf(s, e_tol=1e-9, d_tol=1e-6)
@@ -115,20 +122,36 @@ def evaluate(ctx: hf.Context, model: hf.Model, n_eval: int = 32, waters: int = 3
         t0 = time.perf_counter()
         Pg = predict_or_none(model, s)
         t_pred = time.perf_counter() - t0
+        t0 = time.perf_counter()
         learned = hf.scf(s, e_tol=1e-9, d_tol=1e-6, P_guess=Pg) if Pg is not None else core
-        t_learn = time.perf_counter() - t0
-        rows.append({"cluster": m, "core_iterations": core["iterations"], "core_s": t_core,
-                     "learned_iterations": learned["iterations"], "learned_s": t_learn, "predict_s": t_pred,
-                     "fallback": Pg is None, "core_energy": core["energy"], "learned_energy": learned["energy"],
-                     "abs_dE": abs(core["energy"] - learned["energy"])})
+        t_learn = time.perf_counter() - t0 + t_pred
         s.close()
+        t0 = time.perf_counter()
+        sm = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=prim_tau, fp32_cutoff=fp32_cutoff)
+        setup_mixed = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        mixed = hf.scf(sm, e_tol=1e-9, d_tol=1e-6, P_guess=Pg)
+        t_mixed = time.perf_counter() - t0 + t_pred
+        sm.close()
+        rows.append({"cluster": m, "core_iterations": core["iterations"], "core_s": t_core,
+                     "learned_iterations": learned["iterations"], "learned_s": t_learn,
+                     "mixed_learned_iterations": mixed["iterations"], "mixed_learned_s": t_mixed,
+                     "mixed_learned_mixed_iterations": mixed["mixed_iterations"],
+                     "predict_s": t_pred, "setup_fp64_s": setup64, "setup_mixed_s": setup_mixed,
+                     "fallback": Pg is None, "core_energy": core["energy"], "learned_energy": learned["energy"],
+                     "mixed_learned_energy": mixed["energy"],
+                     "abs_dE": abs(core["energy"] - learned["energy"]),
+                     "abs_dE_mixed": abs(core["energy"] - mixed["energy"])})
         if log:
-            log(f"eval {m}: core {core['iterations']} it {t_core:.2f} s, learned {learned['iterations']} it "
-                f"{t_learn:.2f} s, |dE| {rows[-1]['abs_dE']:.2e}")
+            log(f"eval {m}: core {core['iterations']} it {t_core:.2f} s | learned {learned['iterations']} it "
+                f"{t_learn:.2f} s | mixed+learned {mixed['iterations']} it {t_mixed:.2f} s | "
+                f"|dE| {rows[-1]['abs_dE']:.1e} {rows[-1]['abs_dE_mixed']:.1e}")
+    mean = lambda k: float(np.mean([r[k] for r in rows]))  # noqa: E731
     return {"rows": rows,
-            "mean_core_iterations": float(np.mean([r["core_iterations"] for r in rows])),
-            "mean_learned_iterations": float(np.mean([r["learned_iterations"] for r in rows])),
-            "mean_core_s": float(np.mean([r["core_s"] for r in rows])),
-            "mean_learned_s": float(np.mean([r["learned_s"] for r in rows])),
+            "mean_core_iterations": mean("core_iterations"), "mean_learned_iterations": mean("learned_iterations"),
+            "mean_mixed_learned_iterations": mean("mixed_learned_iterations"),
+            "mean_core_s": mean("core_s"), "mean_learned_s": mean("learned_s"),
+            "mean_mixed_learned_s": mean("mixed_learned_s"),
             "max_abs_dE": float(max(r["abs_dE"] for r in rows)),
+            "max_abs_dE_mixed": float(max(r["abs_dE_mixed"] for r in rows)),
             "fallbacks": int(sum(r["fallback"] for r in rows))}
