@@ -71,6 +71,14 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """Largest value of x over all ranks (the bench's max-over-ranks timing)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def random_density(S, n_occ, cfg, idx):
     """P = 2 C C^T with C = G L^-T, L L^T = G^T S G (input preparation, untimed)."""
     import numpy as np
@@ -179,9 +187,7 @@ def run_ours(a):
     clk = clocks.stop()
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max(total_ms, dist, dev)
         dist.barrier()
     value = world * a.steps / (total_ms / 1e3)
 
@@ -198,9 +204,7 @@ def run_ours(a):
             sysm.fock_build(Ph.numpy(), F=Fh.numpy())
         dt = time.perf_counter() - t0
         if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+            dt = reduce_max(dt, dist, dev)
         e2e = {"value": world * a.steps / dt, "unit": "Fock builds/s", "h2d_bytes_per_step": N * N * 8,
                "d2h_bytes_per_step": N * N * 8 + 8}
 

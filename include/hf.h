@@ -187,6 +187,17 @@ int hf_one_electron(hf_system* sys, double* S, double* H, int flags);
 int hf_fock_build(hf_system* sys, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
                   int flags);
 
+/* One shard of the Fock build for multi-device or multi-process use: the
+ * quartets [n s / S, n (s+1) / S) of every angular-class launch (n = that
+ * launch's screened quartet count), giving partial J and K.  The sum over
+ * s = 0..S-1 of the partial J (K) is the full J (K), so F = H + sum_s J_s -
+ * 1/2 sum_s K_s: the counterpart of the paper's per-rank partial Fock matrix
+ * and ddi_gsumf (Algorithms 1-3), with the sum left to the caller (for
+ * example one allreduce of J and K).  J, K: [N*N] outputs (required).
+ * flags: HF_PTR_DEVICE, HF_FP64_ONLY.  Errors: HF_E_INVALID (bad shard,
+ * NULL pointer, P not finite or not symmetric), HF_E_CUDA. */
+int hf_fock_build_partial(hf_system* sys, const double* P, int shard, int n_shards, double* J, double* K, int flags);
+
 /* ------------------------------------------------------------------- SCF */
 
 /* Options of hf_scf_run (zero-initialise, then set what differs):

@@ -675,4 +675,80 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
     return HF_OK;
 }
 
+
+// One shard of the Fock build: the quartets [n s / S, n (s+1) / S) of every class launch.
+int hf_fock_build_partial(hf_system* S, const double* P, int shard, int n_shards, double* J, double* K, int flags)
+{
+    if (!S || !P || !J || !K) return fail(HF_E_INVALID, "hf_fock_build_partial: NULL argument");
+    if (n_shards < 1 || shard < 0 || shard >= n_shards) return fail(HF_E_INVALID, "hf_fock_build_partial: bad shard");
+    DeviceGuard g(S->ctx->device);
+    hf_ctx* ctx = S->ctx;
+    hf_system& X = *S;
+    cudaStream_t st = ctx->stream;
+    const int N = S->n_bf;
+    const size_t NN = (size_t)N * N;
+    const bool dev = (flags & HF_PTR_DEVICE) != 0;
+    const double* dP = P;
+    if (!dev) {
+        HF_CUDA(cudaMemcpyAsync(X.staging_P.p, P, NN * sizeof(double), cudaMemcpyHostToDevice, st));
+        dP = X.staging_P.as<double>();
+    }
+    HF_CUDA(cudaMemsetAsync(X.bad.p, 0, sizeof(int), st));
+    KCHK(launch_scale_density(N, dP, S->comp_norm.as<double>(), S->P64.as<double>(),
+                              S->P32.p ? S->P32.as<float>() : nullptr, X.bad.as<int>(), st));
+    int bad = 0;
+    HF_CUDA(cudaMemcpyAsync(&bad, X.bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));
+    if (bad) return fail(HF_E_INVALID, "hf_fock_build_partial: density is not finite or not symmetric");
+    HF_CUDA(cudaMemsetAsync(S->Jt.p, 0, NN * sizeof(double), st));
+    HF_CUDA(cudaMemsetAsync(S->Kt.p, 0, NN * sizeof(double), st));
+    EriArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pairs = S->pairs.as<PairHdr>();
+    a.prims64 = S->prims64.p;
+    a.prims32 = S->prims32.p;
+    a.N = N;
+    a.P64 = S->P64.as<double>();
+    a.P32 = S->P32.p ? S->P32.as<float>() : nullptr;
+    a.Jt = S->Jt.as<double>();
+    a.Kt = S->Kt.as<double>();
+    a.boys64 = ctx->boys64.as<double>();
+    a.boys32 = ctx->boys32.as<float>();
+    a.prim_tau = S->th.prim_tau;
+    for (int ci = 0; ci < kNumClasses; ci++) {
+        const auto& pl = S->plan[ci];
+        const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
+        a.bra = S->class_ids[Xc].as<int>();
+        a.ket = S->class_ids[Yc].as<int>();
+        a.n_bra = S->class_count[Xc];
+        a.same = Xc == Yc;
+        for (int prec = 0; prec < 2; prec++) {
+            const long long n = prec ? pl.n32 : pl.n64;
+            const long long q0 = n * shard / n_shards, q1 = n * (shard + 1) / n_shards;
+            if (q1 <= q0) continue;
+            a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
+            a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
+            a.q_begin = q0;
+            a.n_quartets = q1;
+            const int use_f32 = prec && !(flags & HF_FP64_ONLY);
+            const int lanes = (!use_f32 && q1 - q0 < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
+            const long long blocks = ((q1 - q0) * lanes + kEriThreads - 1) / kEriThreads;
+            const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
+            kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st, lanes);
+            HF_CUDA(cudaGetLastError());
+        }
+    }
+    // J and K of this shard (no H): assembly with a zero core Hamiltonian is F = J - K/2; use the
+    // F output of the assembly kernel only as scratch
+    double* dJ = dev ? J : X.staging_out.as<double>();
+    double* dK = dev ? K : X.staging_out.as<double>() + NN;
+    KCHK(launch_assemble(N, S->Jt.as<double>(), S->Kt.as<double>(), S->comp_norm.as<double>(), S->H.as<double>(), dJ,
+                         dK, S->F.as<double>(), st));
+    if (!dev) {
+        HF_CUDA(cudaMemcpyAsync(J, dJ, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HF_CUDA(cudaMemcpyAsync(K, dK, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    HF_CUDA(cudaStreamSynchronize(st));
+    return HF_OK;
+}
 }  // extern "C"

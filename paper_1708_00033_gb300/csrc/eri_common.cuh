@@ -163,7 +163,7 @@ constexpr int kEriThreads = 128;
         const int grp = (threadIdx.x & 31) / GK;                                                             \
         const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                      \
         const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;                                   \
-        for (long long wb = warp * gpw; wb < a.n_quartets; wb += nwarps * gpw) { /* warp-uniform */          \
+        for (long long wb = a.q_begin + warp * gpw; wb < a.n_quartets; wb += nwarps * gpw) { /* warp-uniform */ \
             const long long q = wb + grp;                                                                    \
             const bool valid = q < a.n_quartets;                                                             \
             PairHdr hb, hk;                                                                                  \

@@ -45,6 +45,7 @@ struct EriArgs {
     const float* boys32;
     double prim_tau;                  // skip primitive quartets with B_ab * B_cd < prim_tau
     unsigned long long* prim_count;   // evaluated primitive quartets (nullptr: not counted)
+    long long q_begin;                // first quartet of this launch (quartets [q_begin, n_quartets))
 };
 
 struct SchwarzArgs {

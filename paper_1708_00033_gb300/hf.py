@@ -135,6 +135,7 @@ def load_library():
     lib.hf_fock_build.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Stats_c),
                                   ctypes.c_int]
     lib.hf_fock_build_noalloc.argtypes = [vp, vp, vp, vp, vp]
+    lib.hf_fock_build_partial.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int]
     lib.hf_scf_run.argtypes = [vp, ctypes.POINTER(ScfOpts_c), vp, vp, vp, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ScfResult_c), ctypes.c_int]
     lib.hf_eigh.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_int]
@@ -481,6 +482,27 @@ def fock_build_noalloc(system: "System", P, F, J=None, K=None):
     ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
     _check(load_library().hf_fock_build_noalloc(system._h, ptr(P), ptr(F), ptr(J), ptr(K)), "hf_fock_build_noalloc")
     return F
+
+
+def fock_build_partial(system: "System", P, shard: int, n_shards: int):
+    """hf_fock_build_partial on host arrays: (J_shard, K_shard)."""
+    N = system.n_bf
+    P = _as_f64(P)
+    J, K = np.empty((N, N)), np.empty((N, N))
+    _check(load_library().hf_fock_build_partial(system._h, P.ctypes.data, int(shard), int(n_shards), J.ctypes.data,
+                                                K.ctypes.data, HF_PTR_HOST), "hf_fock_build_partial")
+    return J, K
+
+
+def assemble_shards(H, J_part, K_part, all_reduce_sum):
+    """F = H + sum_r J_r - 1/2 sum_r K_r from this rank's partial J and K.
+
+    ``all_reduce_sum`` sums an array over the ranks (for example an NCCL or
+    gloo allreduce); this is the reduction the paper performs with ddi_gsumf.
+    Returns (F, J, K)."""
+    J = all_reduce_sum(J_part)
+    K = all_reduce_sum(K_part)
+    return H + J - 0.5 * K, J, K
 
 
 def stats_dict(st: Stats_c) -> dict:

@@ -160,3 +160,24 @@ def test_primitive_screening_parity(ctx, oracle_mod, prim_tau):
     assert st["prim_quartets_fp64"] < 81 * st["quartets_fp64"]
     assert np.abs(out["J"] - J).max() <= 1e-10
     assert np.abs(out["K"] - K).max() <= 1e-10
+
+
+@pytest.mark.parametrize("n_shards", [2, 3])
+def test_shards_sum_to_full_build(ctx, oracle_mod, n_shards):
+    """hf_fock_build_partial over all shards equals one full build (the
+    per-rank partial Fock matrices of the paper's distributed algorithms)."""
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(4, I.CONFIG_SINGLE_BUILD)
+    basis = I.synthetic_basis(geom)
+    mol = oracle_mod.Molecule(geom, basis)
+    P = _density(oracle_mod, mol, 20, I.CONFIG_SINGLE_BUILD, 0)
+    s = hf.System(ctx, geom, basis, schwarz_tau=1e-10, prim_tau=1e-14)
+    full = s.fock_build(P, want_J=True, want_K=True)
+    parts = [hf.fock_build_partial(s, P, k, n_shards) for k in range(n_shards)]
+    S_, H = s.one_electron()
+    # stand-in for an allreduce over ranks: shard 0's partial matrices summed with the others
+    sums = {id(parts[0][0]): sum(p[0] for p in parts), id(parts[0][1]): sum(p[1] for p in parts)}
+    F, J, K = hf.assemble_shards(H, parts[0][0], parts[0][1], lambda a: sums[id(a)])
+    assert np.abs(J - full["J"]).max() <= 1e-12
+    assert np.abs(K - full["K"]).max() <= 1e-12
+    assert np.abs(F - full["F"]).max() <= 1e-12
