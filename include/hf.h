@@ -53,6 +53,8 @@ extern "C" {
 #define HF_PTR_DEVICE 1 /* matrix arguments are device pointers */
 #define HF_TIMING 2     /* fill the per-kernel device times of hf_stats */
 #define HF_FP64_ONLY 8  /* hf_fock_build: evaluate the FP32 part of a mixed system in FP64 too */
+#define HF_DENSITY_SCREEN 16 /* hf_fock_build_partial: also skip quartets whose Schwarz bound times the
+                                largest |P| of the six density blocks they touch (x4) is below schwarz_tau */
 
 typedef struct hf_ctx hf_ctx;       /* one device + one stream + constant tables */
 typedef struct hf_system hf_system; /* one molecule: basis, pairs, screening plan, 1e matrices */
@@ -194,8 +196,10 @@ int hf_fock_build(hf_system* sys, const double* P, double* F, double* J, double*
  * 1/2 sum_s K_s: the counterpart of the paper's per-rank partial Fock matrix
  * and ddi_gsumf (Algorithms 1-3), with the sum left to the caller (for
  * example one allreduce of J and K).  J, K: [N*N] outputs (required).
- * flags: HF_PTR_DEVICE, HF_FP64_ONLY.  Errors: HF_E_INVALID (bad shard,
- * NULL pointer, P not finite or not symmetric), HF_E_CUDA. */
+ * flags: HF_PTR_DEVICE, HF_FP64_ONLY, HF_DENSITY_SCREEN (density-weighted
+ * Schwarz screening: the J and K of a density difference, as in incremental
+ * SCF builds).  Errors: HF_E_INVALID (bad shard, NULL pointer, P not finite
+ * or not symmetric), HF_E_CUDA. */
 int hf_fock_build_partial(hf_system* sys, const double* P, int shard, int n_shards, double* J, double* K, int flags);
 
 /* ------------------------------------------------------------------- SCF */
@@ -211,7 +215,12 @@ int hf_fock_build_partial(hf_system* sys, const double* P, int shard, int n_shar
  *              mixed FP32/FP64 split until |dE| < mixed_switch (0: 1e-5),
  *              then every later build is FP64 only (HF_FP64_ONLY) and the
  *              DIIS history restarts; convergence is only declared on FP64
- *              builds, so the final energy is that of the plain FP64 method. */
+ *              builds, so the final energy is that of the plain FP64 method.
+ *   incremental  1: between full rebuilds, J and K are updated with the J and
+ *              K of P_k - P_ref (hf_fock_build_partial with HF_DENSITY_SCREEN),
+ *              so small density changes skip most quartets; convergence is
+ *              only declared on a full rebuild.
+ *   rebuild_every  full rebuild period of the incremental mode (0: 8). */
 typedef struct {
     int32_t n_occ;
     int32_t max_iter;
@@ -220,6 +229,8 @@ typedef struct {
     int32_t diis_size;
     int32_t diis_off;
     double mixed_switch;
+    int32_t incremental;
+    int32_t rebuild_every;
 } hf_scf_opts;
 
 /* Result of hf_scf_run. */
@@ -236,7 +247,7 @@ typedef struct {
     int32_t n_kept;         /* orthogonal basis size (N unless near-linear dependence) */
     double s_min;           /* smallest overlap eigenvalue */
     int32_t mixed_iterations; /* builds done with the FP32/FP64 split */
-    int32_t pad;
+    int32_t full_builds;      /* builds from the full density (the rest were incremental) */
 } hf_scf_result;
 
 /* Closed-shell SCF (Section 3, Eq. FC = eSC): X = S^-1/2 (canonical

@@ -715,6 +715,14 @@ int hf_fock_build_partial(hf_system* S, const double* P, int shard, int n_shards
     a.boys64 = ctx->boys64.as<double>();
     a.boys32 = ctx->boys32.as<float>();
     a.prim_tau = S->th.prim_tau;
+    if ((flags & HF_DENSITY_SCREEN) && S->th.schwarz_tau > 0.0) {
+        if (!X.dsh.p) TRY(X.dsh.alloc(sizeof(float) * (size_t)S->n_shells * S->n_shells));
+        KCHK(launch_shell_block_max(S->n_shells, N, S->sh_l.as<int>(), S->sh_bf0.as<int>(), dP, X.dsh.as<float>(),
+                                    st));
+        a.dsh = X.dsh.as<float>();
+        a.n_sh = S->n_shells;
+        a.dtau = (float)S->th.schwarz_tau;
+    }
     for (int ci = 0; ci < kNumClasses; ci++) {
         const auto& pl = S->plan[ci];
         const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;

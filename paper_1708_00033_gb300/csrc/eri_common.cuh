@@ -145,6 +145,19 @@ __device__ __forceinline__ int find_bra(const long long* __restrict__ off, int n
 
 constexpr int kEriThreads = 128;
 
+// Density-weighted Schwarz test: a quartet (AB|CD) changes the six Fock blocks of Eq. 1a-1f by at most
+// Q_AB Q_CD times the largest |P| of the blocks (CD), (AB), (BD), (AC), (BC), (AD) it is contracted with
+// (times 4 for the Coulomb weight); it is skipped when that bound is below dtau.
+template <typename A>
+__device__ __forceinline__ bool density_screen_passes(const A& a, const PairHdr& hb, const PairHdr& hk)
+{
+    const int n = a.n_sh;
+    const float* d = a.dsh;
+    float m = fmaxf(fmaxf(d[hk.A * n + hk.B], d[hb.A * n + hb.B]), fmaxf(d[hb.B * n + hk.B], d[hb.A * n + hk.A]));
+    m = fmaxf(m, fmaxf(d[hb.B * n + hk.A], d[hb.A * n + hk.B]));
+    return 4.0f * (float)(hb.Q * hk.Q) * m >= a.dtau;
+}
+
 }  // namespace hf
 
 // Kernels and host launchers of one class.  The digestion weight of a unique
@@ -179,8 +192,9 @@ constexpr int kEriThreads = 128;
             } else {                                                                                         \
                 hb = hk = a.pairs[a.bra[0]];                                                                 \
             }                                                                                                \
+            const bool live = valid && (!a.dsh || density_screen_passes(a, hb, hk));                         \
             nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, a.Jt, a.Kt, nullptr, ptau, lane,   \
-                                               valid);                                                       \
+                                               live);                                                        \
         }                                                                                                    \
         if (a.prim_count) {                                                                                  \
             const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \

@@ -71,6 +71,41 @@ __global__ void k_energy_final(int nb, const double* __restrict__ partial, doubl
     if (threadIdx.x == 0) *out = 0.5 * sm[0];
 }
 
+// dsh[i][j] = max |P_mu nu| over the (i, j) shell block
+__global__ void k_shell_block_max(int n_sh, int N, const int* __restrict__ l, const int* __restrict__ bf0,
+                                  const double* __restrict__ P, float* __restrict__ dsh)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_sh * n_sh) return;
+    const int i = (int)(t / n_sh), j = (int)(t % n_sh);
+    const int ni = (l[i] + 1) * (l[i] + 2) / 2, nj = (l[j] + 1) * (l[j] + 2) / 2;
+    double m = 0.0;
+    for (int a = 0; a < ni; a++)
+        for (int b = 0; b < nj; b++) m = fmax(m, fabs(P[(size_t)(bf0[i] + a) * N + bf0[j] + b]));
+    dsh[t] = (float)m;
+}
+
+int launch_shell_block_max(int n_sh, int N, const int* l, const int* bf0, const double* P, float* dsh, cudaStream_t s)
+{
+    const long long n = (long long)n_sh * n_sh;
+    if (n > 0) k_shell_block_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_sh, N, l, bf0, P, dsh);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// C = A + alpha * B (N x N)
+__global__ void k_axpby(long long n, const double* __restrict__ A, double alpha, const double* __restrict__ B,
+                        double* __restrict__ C)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) C[t] = A[t] + alpha * B[t];
+}
+
+int launch_axpby(long long n, const double* A, double alpha, const double* B, double* C, cudaStream_t s)
+{
+    if (n > 0) k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, A, alpha, B, C);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_scale_density(int N, const double* P, const double* comp_norm, double* P64, float* P32, int* bad,
                          cudaStream_t s)
 {

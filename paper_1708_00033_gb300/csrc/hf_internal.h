@@ -46,6 +46,9 @@ struct EriArgs {
     double prim_tau;                  // skip primitive quartets with B_ab * B_cd < prim_tau
     unsigned long long* prim_count;   // evaluated primitive quartets (nullptr: not counted)
     long long q_begin;                // first quartet of this launch (quartets [q_begin, n_quartets))
+    const float* dsh;                 // [n_sh x n_sh] max |P| per shell block (nullptr: no density screening)
+    int n_sh;
+    float dtau;                       // density-weighted screening threshold
 };
 
 struct SchwarzArgs {
@@ -178,6 +181,7 @@ struct hf_system {
     hf::DevBuf class_q[hf::kNumPairClasses];  // sorted bounds of class_ids
     hf::DevBuf Qall, counts, staging_P, staging_out, bad, Bprim, prim_count;
     hf::DevBuf arena_in, arena_mat, arena_sched;  // owners of the views above
+    hf::DevBuf dsh;                                // density block maxima for density-weighted screening
     int maxpp = 0;
     // host copies used by the learned guess: nuclear charges, first basis
     // function and function count of each atom (-1 if its shells are not contiguous)

@@ -15,6 +15,7 @@
 
 #include "hf_internal.h"
 #include "linalg.cuh"
+#include "setup.cuh"
 
 namespace hf {
 namespace {
@@ -129,7 +130,9 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
         if (o.diis_size == 0 && !o.diis_off) o.diis_size = 8;
         if (o.diis_off) o.diis_size = 0;
         if (o.mixed_switch == 0.0) o.mixed_switch = 1e-5;
+        if (o.rebuild_every <= 0) o.rebuild_every = 8;
     }
+    if (!opts_in) o.rebuild_every = 8;
     if (!opts_in) o.mixed_switch = 1e-5;
     bool mixed = S->th.fp32_cutoff > 0.0;
     const int N = S->n_bf;
@@ -260,14 +263,53 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
     // --------------------------------------------------------- iterations
     double E_old = 0.0, E = 0.0, dP = 0.0;
     int it = 0, converged = 0, nh = 0, head = 0;
+    DevBuf Jacc, Kacc, Pref, Dd, Jd, Kd;
+    if (o.incremental) {
+        S_TRY(Jacc.alloc(NN * sizeof(double)));
+        S_TRY(Kacc.alloc(NN * sizeof(double)));
+        S_TRY(Pref.alloc(NN * sizeof(double)));
+        S_TRY(Dd.alloc(NN * sizeof(double)));
+        S_TRY(Jd.alloc(NN * sizeof(double)));
+        S_TRY(Kd.alloc(NN * sizeof(double)));
+    }
+    int since_full = 0;
+    bool force_full = true;
     std::vector<const double*> fptr(m_diis), eptr(m_diis);
     for (it = 1; it <= o.max_iter; it++) {
         double E_el = 0.0;
         const double tf = now_s();
         double* Fslot = Fh[head].as<double>();
-        int rc = hf_fock_build(S, P.as<double>(), Fslot, nullptr, nullptr, &E_el, nullptr,
-                               HF_PTR_DEVICE | (mixed ? 0 : HF_FP64_ONLY));
-        if (rc != HF_OK) return rc;
+        const int pflags = HF_PTR_DEVICE | (mixed ? 0 : HF_FP64_ONLY);
+        bool full = true;
+        int rc;
+        if (!o.incremental) {
+            rc = hf_fock_build(S, P.as<double>(), Fslot, nullptr, nullptr, &E_el, nullptr, pflags);
+            if (rc != HF_OK) return rc;
+        } else {
+            full = force_full || since_full >= o.rebuild_every;
+            if (full) {  // J, K of the full density
+                rc = hf_fock_build_partial(S, P.as<double>(), 0, 1, Jacc.as<double>(), Kacc.as<double>(), pflags);
+                if (rc != HF_OK) return rc;
+                since_full = 0;
+                res->full_builds++;
+            } else {  // J, K += J, K of the density change, density-weighted screening
+                S_K(launch_axpby((long long)NN, P.as<double>(), -1.0, Pref.as<double>(), Dd.as<double>(), st));
+                rc = hf_fock_build_partial(S, Dd.as<double>(), 0, 1, Jd.as<double>(), Kd.as<double>(),
+                                           pflags | HF_DENSITY_SCREEN);
+                if (rc != HF_OK) return rc;
+                S_K(launch_axpby((long long)NN, Jacc.as<double>(), 1.0, Jd.as<double>(), Jacc.as<double>(), st));
+                S_K(launch_axpby((long long)NN, Kacc.as<double>(), 1.0, Kd.as<double>(), Kacc.as<double>(), st));
+                since_full++;
+            }
+            force_full = false;
+            HF_CUDA(cudaMemcpyAsync(Pref.p, P.p, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            // F = H + J - K/2 and E_elec = 1/2 sum P (H + F)
+            S_K(launch_axpby((long long)NN, S->H.as<double>(), 1.0, Jacc.as<double>(), Fslot, st));
+            S_K(launch_axpby((long long)NN, Fslot, -0.5, Kacc.as<double>(), Fslot, st));
+            S_K(launch_energy(N, P.as<double>(), S->H.as<double>(), Fslot, part.as<double>(), scal.as<double>() + 8, st));
+            HF_CUDA(cudaMemcpyAsync(&E_el, scal.as<double>() + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+            HF_CUDA(cudaStreamSynchronize(st));
+        }
         t_fock += now_s() - tf;
         E = E_el + S->E_nn;
         if (energies) energies[it - 1] = E;
@@ -312,12 +354,16 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
         res->last_dE = it > 1 ? fabs(E - E_old) : INFINITY;
         res->last_dP = dP;
         if (!mixed && it > 1 && fabs(E - E_old) < o.e_tol && dP < o.d_tol) {
-            converged = 1;
-            break;
+            if (full) {
+                converged = 1;
+                break;
+            }
+            force_full = true;  // confirm on a build from the full density
         }
         if (mixed && it > 1 && fabs(E - E_old) < o.mixed_switch) {
             mixed = false;  // switch to FP64-only builds; the mixed-phase Fock matrices leave the DIIS history
             nh = 0;
+            force_full = true;  // and the accumulated J, K are rebuilt in FP64
         }
         E_old = E;
         std::swap(P.p, Pn.p);
@@ -325,6 +371,7 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
     if (it > o.max_iter) it = o.max_iter;
     res->energy = E;
     res->iterations = it;
+    if (!o.incremental) res->full_builds = it;
     res->converged = converged;
     res->jacobi_sweeps = sweeps;
     res->seconds_fock = t_fock;

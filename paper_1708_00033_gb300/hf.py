@@ -27,6 +27,8 @@ HF_E_NOCONV = -6
 HF_PTR_HOST = 0
 HF_PTR_DEVICE = 1
 HF_TIMING = 2
+HF_FP64_ONLY = 8
+HF_DENSITY_SCREEN = 16
 NUM_CLASSES = 21
 
 CLASS_NAMES = []
@@ -79,7 +81,7 @@ class SystemInfo_c(ctypes.Structure):
 class ScfOpts_c(ctypes.Structure):
     _fields_ = [("n_occ", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("e_tol", ctypes.c_double),
                 ("d_tol", ctypes.c_double), ("diis_size", ctypes.c_int32), ("diis_off", ctypes.c_int32),
-                ("mixed_switch", ctypes.c_double)]
+                ("mixed_switch", ctypes.c_double), ("incremental", ctypes.c_int32), ("rebuild_every", ctypes.c_int32)]
 
 
 class ScfResult_c(ctypes.Structure):
@@ -87,7 +89,7 @@ class ScfResult_c(ctypes.Structure):
                 ("converged", ctypes.c_int32), ("last_dE", ctypes.c_double), ("last_dP", ctypes.c_double),
                 ("seconds_total", ctypes.c_double), ("seconds_fock", ctypes.c_double),
                 ("seconds_diag", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int32), ("n_kept", ctypes.c_int32),
-                ("s_min", ctypes.c_double), ("mixed_iterations", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("s_min", ctypes.c_double), ("mixed_iterations", ctypes.c_int32), ("full_builds", ctypes.c_int32)]
 
 
 class BatchInfo_c(ctypes.Structure):
@@ -447,11 +449,12 @@ def guess_predict(model: Model, system: "System") -> np.ndarray:
 
 
 def scf(system: "System", n_occ: int = 0, max_iter: int = 100, e_tol: float = 1e-9, d_tol: float = 1e-6,
-        diis_size: int = 8, P_guess=None, raise_on_noconv: bool = True, mixed_switch: float = 1e-5) -> dict:
+        diis_size: int = 8, P_guess=None, raise_on_noconv: bool = True, mixed_switch: float = 1e-5,
+        incremental: bool = False, rebuild_every: int = 8) -> dict:
     """hf_scf_run with host arrays; returns energy, density, orbital energies and timings."""
     N = system.n_bf
     o = ScfOpts_c(int(n_occ), int(max_iter), float(e_tol), float(d_tol), int(diis_size), 1 if diis_size == 0 else 0,
-                  float(mixed_switch))
+                  float(mixed_switch), 1 if incremental else 0, int(rebuild_every))
     P_out = np.empty((N, N))
     eps = np.zeros(N)
     en = np.zeros(max_iter)
@@ -484,13 +487,16 @@ def fock_build_noalloc(system: "System", P, F, J=None, K=None):
     return F
 
 
-def fock_build_partial(system: "System", P, shard: int, n_shards: int):
-    """hf_fock_build_partial on host arrays: (J_shard, K_shard)."""
+def fock_build_partial(system: "System", P, shard: int = 0, n_shards: int = 1, density_screen: bool = False,
+                       fp64_only: bool = False):
+    """hf_fock_build_partial on host arrays: (J_shard, K_shard).  density_screen also skips quartets whose
+    Schwarz bound times the largest |P| of the six blocks they touch is below the Schwarz threshold."""
     N = system.n_bf
     P = _as_f64(P)
     J, K = np.empty((N, N)), np.empty((N, N))
+    flags = HF_PTR_HOST | (HF_DENSITY_SCREEN if density_screen else 0) | (HF_FP64_ONLY if fp64_only else 0)
     _check(load_library().hf_fock_build_partial(system._h, P.ctypes.data, int(shard), int(n_shards), J.ctypes.data,
-                                                K.ctypes.data, HF_PTR_HOST), "hf_fock_build_partial")
+                                                K.ctypes.data, flags), "hf_fock_build_partial")
     return J, K
 
 

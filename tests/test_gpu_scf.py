@@ -92,3 +92,21 @@ def test_scf_reports_nonconvergence(ctx):
     s = hf.System(ctx, geom, basis)
     r = hf.scf(s, max_iter=2, raise_on_noconv=False)
     assert r["status"] == hf.HF_E_NOCONV and not r["converged"] and r["iterations"] == 2
+
+
+@pytest.mark.parametrize("rebuild_every", [3, 8])
+def test_incremental_scf_matches_plain(ctx, rebuild_every):
+    """Incremental SCF (J, K accumulated from density-screened builds of
+    P_k - P_ref, full rebuild every few iterations and before convergence is
+    declared) converges to the plain SCF's energy and density."""
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(8, 2, 3)
+    basis = I.synthetic_basis(geom)
+    s = hf.System(ctx, geom, basis, schwarz_tau=1e-10)
+    plain = hf.scf(s)
+    inc = hf.scf(s, incremental=True, rebuild_every=rebuild_every)
+    assert plain["converged"] and inc["converged"]
+    assert plain["full_builds"] == plain["iterations"]
+    assert 1 <= inc["full_builds"] < inc["iterations"]
+    assert abs(inc["energy"] - plain["energy"]) < 1e-8
+    assert np.abs(inc["P"] - plain["P"]).max() < 1e-5
