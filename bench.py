@@ -45,12 +45,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--prim-tau", type=float, default=1e-14)
-    ap.add_argument("--mode", default="fock", choices=["fock", "scf", "mixed", "batch", "guess"])
+    ap.add_argument("--mode", default="fock", choices=["fock", "scf", "mixed", "batch", "guess", "copies", "peaks"])
     ap.add_argument("--n-train", type=int, default=2000)
     ap.add_argument("--n-eval", type=int, default=32)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--n-mol", type=int, default=512)
     ap.add_argument("--scf-variants", default="fp64,mixed,fp64_incremental,mixed_incremental")
+    ap.add_argument("--copies", default="1,8,152,608", help="accumulator copies compared by --mode copies")
+    ap.add_argument("--copies-workloads", default="4:0,16:1e-10,64:1e-10", help="waters:schwarz_tau list")
     a = ap.parse_args()
     if a.mode == "mixed" and "--waters" not in sys.argv:
         a.waters, a.config_id = 256, 3
@@ -488,6 +490,75 @@ def run_guess(a):
     print(json.dumps(line), flush=True)
 
 
+def run_copies(a):
+    """Shared vs private Fock accumulators (the paper's Table 3 comparison on GPU thread blocks): FP64 build
+    time per accumulator-copy count, per workload, with the device memory the copies take."""
+    import numpy as np
+    import torch
+    from paper_1708_00033_gb300 import hf, inputs
+    ctx = hf.Context(0)
+    copies = [int(c) for c in a.copies.split(",")]
+    rows = []
+    for item in a.copies_workloads.split(","):
+        nw, tau = item.split(":")
+        nw, tau = int(nw), float(tau)
+        cfg = inputs.CONFIG_SINGLE_BUILD if nw == 4 else a.config_id
+        geom = inputs.water_cluster(nw, cfg, 0)
+        basis = inputs.synthetic_basis(geom)
+        s = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=a.prim_tau)
+        S, _ = s.one_electron()
+        Pd = torch.from_numpy(random_density(S, inputs.n_electrons(geom) // 2, cfg, 0)).cuda()
+        Fd = torch.empty_like(Pd)
+        ref = None
+        steps = max(1, a.steps)
+        for c in copies:
+            s.set_fock_copies(c)
+            s.fock_build(Pd, F=Fd)  # warm-up
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.fock_build(Pd, F=Fd)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            F = Fd.cpu().numpy()
+            if ref is None:
+                ref = F
+            rows.append({"waters": nw, "n_bf": s.n_bf, "schwarz_tau": tau, "copies": c,
+                         "ms_median": float(np.median(ms)), "ms": ms,
+                         "copy_bytes": 0 if c == 1 else 2 * c * s.n_bf * s.n_bf * 8,
+                         "max_abs_dF_vs_shared": float(np.abs(F - ref).max())})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        s.close()
+    line = {"metric": "FP64 Fock build time, shared vs private accumulators", "unit": "ms", "value": None,
+            "higher_is_better": False, "n_gpus": 1, "steps": a.steps, "warmup": 1, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "water clusters, random S-orthonormal density",
+                                            "prim_tau": a.prim_tau},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_peaks(a):
+    """The roofline denominators measured by the library's own microbenchmarks, with clocks sampled."""
+    from paper_1708_00033_gb300 import hf
+    ctx = hf.Context(0)
+    hf.measure_peaks(ctx)  # warm-up
+    clk = ClockSampler(0)
+    clk.start()
+    runs = [hf.measure_peaks(ctx) for _ in range(max(1, a.steps))]
+    clocks = clk.stop()
+    best = {k: max(r[k] for r in runs) for k in runs[0]}
+    derived = best["num_sms"] * 2 * 2 * best["sm_max_mhz"] * 1e-3
+    line = {"metric": "device peaks (microbenchmarks)", "unit": "GFLOP/s | Gop/s", "value": best["fp64_fma_gflops"],
+            "higher_is_better": True, "n_gpus": 1, "steps": len(runs), "warmup": 1, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "FMA chains on every SM; FP64 atomic adds into 8 MB"},
+            "best": best, "runs": runs, "fp64_fma_derived_gflops": derived,
+            "fp32_to_fp64_ratio": best["fp32_fma_gflops"] / best["fp64_fma_gflops"], "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -500,6 +571,10 @@ def main():
         run_batch(a)
     elif a.mode == "guess":
         run_guess(a)
+    elif a.mode == "copies":
+        run_copies(a)
+    elif a.mode == "peaks":
+        run_peaks(a)
     else:
         run_ours(a)
 

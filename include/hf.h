@@ -189,6 +189,39 @@ int hf_one_electron(hf_system* sys, double* S, double* H, int flags);
 int hf_fock_build(hf_system* sys, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
                   int flags);
 
+/* Device microbenchmarks that give the roofline denominators of the build:
+ * FP64 and FP32 FMA throughput (independent FMA chains on every SM; the ERI
+ * kernels of Section 3's integral step are bound by the FP64 pipe) and FP64
+ * atomic-add throughput into an 8 MB array (the digestion of Eq. 1a-1f),
+ * random and coalesced addresses.  Each figure is the best of three timed
+ * launches after a warm-up, on the context's stream, with CUDA events; it
+ * takes well under a second.  Rates are per second over the whole GPU.
+ * Errors: HF_E_INVALID (NULL argument), HF_E_NOMEM, HF_E_CUDA. */
+typedef struct {
+    double fp64_fma_gflops;
+    double fp32_fma_gflops;
+    double red_add_f64_random_gops;
+    double red_add_f64_coalesced_gops;
+    double sm_max_mhz;
+    int32_t num_sms;
+    int32_t pad;
+} hf_peaks;
+int hf_measure_peaks(hf_ctx* ctx, hf_peaks* out);
+
+/* Accumulators of the ERI digestion (the paper's shared vs private Fock
+ * matrices, Section 3 and Table 3, mapped to GPU thread blocks).
+ *   copies == 1 (default): every thread block adds its quartets' Eq. 1a-1f
+ *     updates into one shared pair of N x N accumulators with FP64 atomics;
+ *   copies  > 1: block b adds into private copy b % copies; the copies are
+ *     summed after the ERI launches.  Costs 2 * copies * N * N * 8 bytes of
+ *     device memory plus zeroing and summing them on every build.
+ * Applies to hf_fock_build, hf_fock_build_partial and hf_scf_run (not to the
+ * batched or allocation-free builds).  Results equal those with one copy up
+ * to the order of FP64 additions.
+ * Errors: HF_E_INVALID (NULL system, copies outside 1..4096), HF_E_NOMEM (the
+ * copies do not fit; the system is left with one shared copy). */
+int hf_system_set_fock_copies(hf_system* sys, int32_t copies);
+
 /* One shard of the Fock build for multi-device or multi-process use: the
  * quartets [n s / S, n (s+1) / S) of every angular-class launch (n = that
  * launch's screened quartet count), giving partial J and K.  The sum over

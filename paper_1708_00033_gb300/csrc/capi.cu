@@ -554,6 +554,61 @@ int hf_one_electron(hf_system* S, double* Sout, double* Hout, int flags)
     return HF_OK;
 }
 
+// Accumulators of one build: the system's Jt / Kt (one copy shared by every block, updated with FP64
+// atomics), or fock_copies zeroed copies of each, block b writing copy b % fock_copies, summed into
+// Jt / Kt after the ERI launches (the GPU analogue of the paper's private Fock matrices).
+static int begin_accumulate(hf_system& X, EriArgs& a, cudaStream_t st)
+{
+    const size_t NN = (size_t)X.n_bf * X.n_bf;
+    if (X.fock_copies > 1) {
+        HF_CUDA(cudaMemsetAsync(X.copies.p, 0, 2 * (size_t)X.fock_copies * NN * sizeof(double), st));
+        a.Jt = X.copies.as<double>();
+        a.Kt = a.Jt + (size_t)X.fock_copies * NN;
+        a.n_copies = X.fock_copies;
+        a.copy_stride = (long long)NN;
+    } else {
+        HF_CUDA(cudaMemsetAsync(X.Jt.p, 0, NN * sizeof(double), st));
+        HF_CUDA(cudaMemsetAsync(X.Kt.p, 0, NN * sizeof(double), st));
+        a.Jt = X.Jt.as<double>();
+        a.Kt = X.Kt.as<double>();
+        a.n_copies = 1;
+        a.copy_stride = 0;
+    }
+    return HF_OK;
+}
+
+static int end_accumulate(hf_system& X, cudaStream_t st)
+{
+    if (X.fock_copies <= 1) return HF_OK;
+    const long long NN = (long long)X.n_bf * X.n_bf;
+    const double* c = X.copies.as<double>();
+    KCHK(launch_sum_copies(X.fock_copies, NN, c, X.Jt.as<double>(), X.ctx->num_sms, st));
+    KCHK(launch_sum_copies(X.fock_copies, NN, c + (size_t)X.fock_copies * NN, X.Kt.as<double>(), X.ctx->num_sms, st));
+    return HF_OK;
+}
+
+int hf_system_set_fock_copies(hf_system* S, int32_t copies)
+{
+    if (!S) return fail(HF_E_INVALID, "hf_system_set_fock_copies: NULL system");
+    if (copies < 1 || copies > 4096) return fail(HF_E_INVALID, "hf_system_set_fock_copies: copies must be 1..4096");
+    DeviceGuard g(S->ctx->device);
+    HF_CUDA(cudaStreamSynchronize(S->ctx->stream));
+    if (copies == 1) {
+        S->copies.release();
+        S->fock_copies = 1;
+        return HF_OK;
+    }
+    const size_t NN = (size_t)S->n_bf * S->n_bf;
+    S->copies.release();
+    S->fock_copies = 1;
+    if (S->copies.alloc(2 * (size_t)copies * NN * sizeof(double)) != HF_OK) {
+        cudaGetLastError();
+        return fail(HF_E_NOMEM, "hf_system_set_fock_copies: cannot allocate the accumulator copies");
+    }
+    S->fock_copies = copies;
+    return HF_OK;
+}
+
 int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
                   int flags)
 {
@@ -581,19 +636,16 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
     HF_CUDA(cudaStreamSynchronize(st));
     if (bad) return fail(HF_E_INVALID, "hf_fock_build: density is not finite or not symmetric");
     // 2. ERI + digestion, one launch per class and precision
-    HF_CUDA(cudaMemsetAsync(S->Jt.p, 0, NN * sizeof(double), st));
-    HF_CUDA(cudaMemsetAsync(S->Kt.p, 0, NN * sizeof(double), st));
-    if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 1], st));
     EriArgs a;
     memset(&a, 0, sizeof(a));
+    TRY(begin_accumulate(X, a, st));
+    if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 1], st));
     a.pairs = S->pairs.as<PairHdr>();
     a.prims64 = S->prims64.p;
     a.prims32 = S->prims32.p;
     a.N = N;
     a.P64 = S->P64.as<double>();
     a.P32 = S->P32.p ? S->P32.as<float>() : nullptr;
-    a.Jt = S->Jt.as<double>();
-    a.Kt = S->Kt.as<double>();
     a.boys64 = ctx->boys64.as<double>();
     a.boys32 = ctx->boys32.as<float>();
     a.prim_tau = S->th.prim_tau;
@@ -625,6 +677,7 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
             if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * ci + 2 * prec + 1], st));
         }
     }
+    TRY(end_accumulate(X, st));
     if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 2], st));
     // 3. symmetrise and assemble
     double* dF = dev && F ? F : S->F.as<double>();
@@ -666,7 +719,8 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
                 cudaEventElapsedTime(&stats->ms_class_fp32[ci], ctx->ev[4 * ci + 2], ctx->ev[4 * ci + 3]);
             }
         }
-        stats->kernels_launched += 2 + (E_elec ? 2 : 0);  // density scaling, assembly, energy
+        stats->kernels_launched += 2 + (E_elec ? 2 : 0) + (X.fock_copies > 1 ? 2 : 0);  // density scaling,
+                                                                                    // assembly, energy, copy sums
         if (timing) {
             cudaEventElapsedTime(&stats->ms_eri, ctx->ev[4 * kNumClasses + 1], ctx->ev[4 * kNumClasses + 2]);
             cudaEventElapsedTime(&stats->ms_total, ctx->ev[4 * kNumClasses], ctx->ev[4 * kNumClasses + 3]);
@@ -700,18 +754,15 @@ int hf_fock_build_partial(hf_system* S, const double* P, int shard, int n_shards
     HF_CUDA(cudaMemcpyAsync(&bad, X.bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     HF_CUDA(cudaStreamSynchronize(st));
     if (bad) return fail(HF_E_INVALID, "hf_fock_build_partial: density is not finite or not symmetric");
-    HF_CUDA(cudaMemsetAsync(S->Jt.p, 0, NN * sizeof(double), st));
-    HF_CUDA(cudaMemsetAsync(S->Kt.p, 0, NN * sizeof(double), st));
     EriArgs a;
     memset(&a, 0, sizeof(a));
+    TRY(begin_accumulate(X, a, st));
     a.pairs = S->pairs.as<PairHdr>();
     a.prims64 = S->prims64.p;
     a.prims32 = S->prims32.p;
     a.N = N;
     a.P64 = S->P64.as<double>();
     a.P32 = S->P32.p ? S->P32.as<float>() : nullptr;
-    a.Jt = S->Jt.as<double>();
-    a.Kt = S->Kt.as<double>();
     a.boys64 = ctx->boys64.as<double>();
     a.boys32 = ctx->boys32.as<float>();
     a.prim_tau = S->th.prim_tau;
@@ -746,6 +797,7 @@ int hf_fock_build_partial(hf_system* S, const double* P, int shard, int n_shards
             HF_CUDA(cudaGetLastError());
         }
     }
+    TRY(end_accumulate(X, st));
     // J and K of this shard (no H): assembly with a zero core Hamiltonian is F = J - K/2; use the
     // F output of the assembly kernel only as scratch
     double* dJ = dev ? J : X.staging_out.as<double>();

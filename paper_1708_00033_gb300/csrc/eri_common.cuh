@@ -170,6 +170,9 @@ __device__ __forceinline__ bool density_screen_passes(const A& a, const PairHdr&
         const real* P = (const real*)(sizeof(real) == 8 ? (const void*)a.P64 : (const void*)a.P32);          \
         const real* bt = (const real*)(sizeof(real) == 8 ? (const void*)a.boys64 : (const void*)a.boys32);  \
         const float ptau = (float)a.prim_tau;                                                                \
+        const size_t cofs = a.n_copies > 1 ? (size_t)(blockIdx.x % a.n_copies) * a.copy_stride : 0;          \
+        double* const Jt = a.Jt + cofs;                                                                      \
+        double* const Kt = a.Kt + cofs;                                                                      \
         unsigned nprimq = 0;                                                                                 \
         constexpr int gpw = 32 / GK;                                                                         \
         const int lane = threadIdx.x & (GK - 1);                                                             \
@@ -193,7 +196,7 @@ __device__ __forceinline__ bool density_screen_passes(const A& a, const PairHdr&
                 hb = hk = a.pairs[a.bra[0]];                                                                 \
             }                                                                                                \
             const bool live = valid && (!a.dsh || density_screen_passes(a, hb, hk));                         \
-            nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, a.Jt, a.Kt, nullptr, ptau, lane,   \
+            nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, Jt, Kt, nullptr, ptau, lane,       \
                                                live);                                                        \
         }                                                                                                    \
         if (a.prim_count) {                                                                                  \

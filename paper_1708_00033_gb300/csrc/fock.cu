@@ -7,6 +7,8 @@
 //   E_elec = 1/2 sum P (H + F), reduced in a fixed order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "eri_common.cuh"
 #include "setup.cuh"
 
@@ -103,6 +105,25 @@ __global__ void k_axpby(long long n, const double* __restrict__ A, double alpha,
 int launch_axpby(long long n, const double* A, double alpha, const double* B, double* C, cudaStream_t s)
 {
     if (n > 0) k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, A, alpha, B, C);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// out[t] = sum over the copies of in[c * NN + t]: the reduction of per-block accumulator copies
+__global__ void k_sum_copies(int n_copies, long long nn, const double* __restrict__ in, double* __restrict__ out)
+{
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < n_copies; c++) s += in[(size_t)c * nn + t];
+        out[t] = s;
+    }
+}
+
+int launch_sum_copies(int n_copies, long long nn, const double* in, double* out, int num_sms, cudaStream_t s)
+{
+    if (nn > 0) {
+        const long long blocks = std::min<long long>((nn + 255) / 256, (long long)num_sms * 8);
+        k_sum_copies<<<(unsigned)blocks, 256, 0, s>>>(n_copies, nn, in, out);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -49,6 +49,8 @@ struct EriArgs {
     const float* dsh;                 // [n_sh x n_sh] max |P| per shell block (nullptr: no density screening)
     int n_sh;
     float dtau;                       // density-weighted screening threshold
+    int n_copies;                     // > 1: block b accumulates into copy b % n_copies of Jt / Kt
+    long long copy_stride;            // doubles between copies
 };
 
 struct SchwarzArgs {
@@ -182,6 +184,8 @@ struct hf_system {
     hf::DevBuf Qall, counts, staging_P, staging_out, bad, Bprim, prim_count;
     hf::DevBuf arena_in, arena_mat, arena_sched;  // owners of the views above
     hf::DevBuf dsh;                                // density block maxima for density-weighted screening
+    int fock_copies = 1;                           // accumulator copies of Jt / Kt (1: one shared copy)
+    hf::DevBuf copies;                             // [2][fock_copies][N*N] when fock_copies > 1
     int maxpp = 0;
     // host copies used by the learned guess: nuclear charges, first basis
     // function and function count of each atom (-1 if its shells are not contiguous)

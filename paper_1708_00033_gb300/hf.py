@@ -78,6 +78,12 @@ class SystemInfo_c(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class Peaks_c(ctypes.Structure):
+    _fields_ = [("fp64_fma_gflops", ctypes.c_double), ("fp32_fma_gflops", ctypes.c_double),
+                ("red_add_f64_random_gops", ctypes.c_double), ("red_add_f64_coalesced_gops", ctypes.c_double),
+                ("sm_max_mhz", ctypes.c_double), ("num_sms", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class ScfOpts_c(ctypes.Structure):
     _fields_ = [("n_occ", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("e_tol", ctypes.c_double),
                 ("d_tol", ctypes.c_double), ("diis_size", ctypes.c_int32), ("diis_off", ctypes.c_int32),
@@ -138,6 +144,8 @@ def load_library():
                                   ctypes.c_int]
     lib.hf_fock_build_noalloc.argtypes = [vp, vp, vp, vp, vp]
     lib.hf_fock_build_partial.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int]
+    lib.hf_system_set_fock_copies.argtypes = [vp, ctypes.c_int32]
+    lib.hf_measure_peaks.argtypes = [vp, ctypes.POINTER(Peaks_c)]
     lib.hf_scf_run.argtypes = [vp, ctypes.POINTER(ScfOpts_c), vp, vp, vp, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ScfResult_c), ctypes.c_int]
     lib.hf_eigh.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_int]
@@ -234,6 +242,10 @@ class System:
         inf = SystemInfo_c()
         _check(load_library().hf_system_get_info(self._h, ctypes.byref(inf)), "hf_system_get_info")
         return {k: getattr(inf, k) for k, _ in SystemInfo_c._fields_}
+
+    def set_fock_copies(self, copies: int):
+        """hf_system_set_fock_copies: 1 = one shared accumulator pair, >1 = per-block private copies."""
+        _check(load_library().hf_system_set_fock_copies(self._h, int(copies)), "hf_system_set_fock_copies")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -478,6 +490,13 @@ def eigh(ctx: Context, A) -> tuple:
     V = np.empty((n, n))
     _check(load_library().hf_eigh(ctx._h, n, A.ctypes.data, w.ctypes.data, V.ctypes.data, HF_PTR_HOST), "hf_eigh")
     return w, V
+
+
+def measure_peaks(ctx: "Context") -> dict:
+    """hf_measure_peaks: FP64/FP32 FMA and FP64 atomic-add throughput of this GPU."""
+    out = Peaks_c()
+    _check(load_library().hf_measure_peaks(ctx._h, ctypes.byref(out)), "hf_measure_peaks")
+    return {k: getattr(out, k) for k, _ in Peaks_c._fields_ if k != "pad"}
 
 
 def fock_build_noalloc(system: "System", P, F, J=None, K=None):

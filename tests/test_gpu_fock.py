@@ -212,3 +212,30 @@ def test_density_screened_difference_build(ctx, oracle_mod, eps):
     # and the same call without the density test is the plain Schwarz-screened build
     J2, K2 = hf.fock_build_partial(s, dP, fp64_only=True)
     assert np.abs(J2 - J_ref).max() <= 1e-12 and np.abs(K2 - K_ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("copies", [2, 152, 608])
+def test_private_fock_copies(ctx, oracle_mod, copies):
+    """Per-block private accumulator copies (the paper's private Fock
+    matrices) give the shared-accumulator result up to FP64 summation order,
+    and the oracle's within the FP64 tolerance; unscreened 4 waters."""
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(4, I.CONFIG_SINGLE_BUILD)
+    basis = I.synthetic_basis(geom)
+    mol = oracle_mod.Molecule(geom, basis)
+    P = _density(oracle_mod, mol, 20, I.CONFIG_SINGLE_BUILD, 0)
+    s = hf.System(ctx, geom, basis)
+    shared = s.fock_build(P, want_J=True, want_K=True)
+    s.set_fock_copies(copies)
+    priv = s.fock_build(P, want_J=True, want_K=True, stats=True)
+    for k in ("F", "J", "K"):
+        assert np.abs(priv[k] - shared[k]).max() <= 1e-12
+    J, K = mol.jk_unique(P)
+    assert np.abs(priv["J"] - J).max() <= 1e-10 and np.abs(priv["K"] - K).max() <= 1e-10
+    Jp, Kp = hf.fock_build_partial(s, P)
+    assert np.abs(Jp - shared["J"]).max() <= 1e-12 and np.abs(Kp - shared["K"]).max() <= 1e-12
+    s.set_fock_copies(1)
+    again = s.fock_build(P)
+    assert np.abs(again["F"] - shared["F"]).max() <= 1e-12
+    with pytest.raises(hf.HFError):
+        s.set_fock_copies(0)
