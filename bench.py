@@ -347,8 +347,11 @@ def run_scf(a):
         t0 = time.perf_counter()
         sysm = hf.System(ctx, geom, basis, schwarz_tau=a.tau, prim_tau=a.prim_tau, fp32_cutoff=cut)
         setup = time.perf_counter() - t0
-        r = _scf_run(hf, sysm, e_tol=1e-9, d_tol=1e-6, incremental=inc)
-        out[name] = {"energy": r["energy"], "iterations": r["iterations"], "mixed_iterations": r["mixed_iterations"],
+        r = _scf_run(hf, sysm, e_tol=1e-9, d_tol=1e-6, incremental=inc, raise_on_noconv=False)
+        print(f"{name}: converged={r['converged']} it={r['iterations']} full={r['full_builds']} "
+              f"{r['wall_s']:.1f} s E={r['energy']:.10f}", file=sys.stderr, flush=True)
+        out[name] = {"converged": bool(r["converged"]), "energy": r["energy"], "iterations": r["iterations"],
+                     "mixed_iterations": r["mixed_iterations"],
                      "full_builds": r["full_builds"],
                      "scf_s": r["wall_s"], "setup_s": setup, "total_s": r["wall_s"] + setup,
                      "fock_s": r["seconds_fock"], "diag_s": r["seconds_diag"], "jacobi_sweeps": r["jacobi_sweeps"],

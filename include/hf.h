@@ -251,8 +251,10 @@ int hf_fock_build_partial(hf_system* sys, const double* P, int shard, int n_shar
  *              builds, so the final energy is that of the plain FP64 method.
  *   incremental  1: between full rebuilds, J and K are updated with the J and
  *              K of P_k - P_ref (hf_fock_build_partial with HF_DENSITY_SCREEN),
- *              so small density changes skip most quartets; convergence is
- *              only declared on a full rebuild.
+ *              so small density changes skip most quartets.  Once the
+ *              convergence test passes on such a build, every further build
+ *              is a full one and convergence is only declared on a full build
+ *              (so the final energy is that of the plain method).
  *   rebuild_every  full rebuild period of the incremental mode (0: 8). */
 typedef struct {
     int32_t n_occ;

@@ -386,6 +386,7 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
         sa.Q = X.Qall.as<double>();
         sa.boys64 = ctx->boys64.as<double>();
         sa.Bprim = X.Bprim.as<double>();
+        sa.items = X.maxpp + 1;
         kEriClasses[class_index(c, c)].launch_schwarz(sa, kEriThreads, st);
         HF_CUDA(cudaGetLastError());
     }

@@ -145,17 +145,19 @@ __device__ __forceinline__ int find_bra(const long long* __restrict__ off, int n
 
 constexpr int kEriThreads = 128;
 
-// Density-weighted Schwarz test: a quartet (AB|CD) changes the six Fock blocks of Eq. 1a-1f by at most
+// Density-weighted screening: a quartet (AB|CD) changes the six Fock blocks of Eq. 1a-1f by at most
 // Q_AB Q_CD times the largest |P| of the blocks (CD), (AB), (BD), (AC), (BC), (AD) it is contracted with
-// (times 4 for the Coulomb weight); it is skipped when that bound is below dtau.
+// (times 4 for the Coulomb weight); density_block_max returns that largest |P|.  The quartet is skipped
+// when 4 Q_AB Q_CD max|P| is below dtau, and its primitive quartets are screened against prim_tau / max|P|,
+// so that a build from a small density (a difference of densities) keeps the absolute error bound of
+// the build from a density of order one.
 template <typename A>
-__device__ __forceinline__ bool density_screen_passes(const A& a, const PairHdr& hb, const PairHdr& hk)
+__device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb, const PairHdr& hk)
 {
     const int n = a.n_sh;
     const float* d = a.dsh;
     float m = fmaxf(fmaxf(d[hk.A * n + hk.B], d[hb.A * n + hb.B]), fmaxf(d[hb.B * n + hk.B], d[hb.A * n + hk.A]));
-    m = fmaxf(m, fmaxf(d[hb.B * n + hk.A], d[hb.A * n + hk.B]));
-    return 4.0f * (float)(hb.Q * hk.Q) * m >= a.dtau;
+    return fmaxf(m, fmaxf(d[hb.B * n + hk.A], d[hb.A * n + hk.B]));
 }
 
 }  // namespace hf
@@ -195,9 +197,14 @@ __device__ __forceinline__ bool density_screen_passes(const A& a, const PairHdr&
             } else {                                                                                         \
                 hb = hk = a.pairs[a.bra[0]];                                                                 \
             }                                                                                                \
-            const bool live = valid && (!a.dsh || density_screen_passes(a, hb, hk));                         \
-            nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, Jt, Kt, nullptr, ptau, lane,       \
-                                               live);                                                        \
+            bool live = valid;                                                                               \
+            float pt = ptau;                                                                                 \
+            if (a.dsh) { /* density-weighted screening (warp-uniform branch) */                              \
+                const float dm = valid ? density_block_max(a, hb, hk) : 0.0f;                                \
+                live = valid && 4.0f * (float)(hb.Q * hk.Q) * dm >= a.dtau;                                  \
+                pt = ptau / fmaxf(dm, 1e-30f);                                                               \
+            }                                                                                                \
+            nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane, live); \
         }                                                                                                    \
         if (a.prim_count) {                                                                                  \
             const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \
@@ -228,30 +235,35 @@ __device__ __forceinline__ bool density_screen_passes(const A& a, const PairHdr&
         return m;                                                                                            \
     }
 
-// Schwarz bounds of the pairs of a diagonal class: Q = sqrt(max |(ab|ab)|).
+// Schwarz bounds of the pairs of a diagonal class: Q = sqrt(max |(ab|ab)|) of the
+// contracted pair (item 0 of each pair) and B = the same bound of each primitive pair
+// alone (items 1..a.items-1), one thread per item so that the high-L classes'
+// single-thread latency is paid once per pair, not once per primitive pair.
 #define SCHWARZ_KERNEL(NAME)                                                                                 \
     __global__ void __launch_bounds__(kEriThreads) k_schwarz_##NAME(const SchwarzArgs a)                    \
     {                                                                                                        \
-        const int t = blockIdx.x * blockDim.x + threadIdx.x;                                                 \
-        if (t >= a.n) return;                                                                                \
-        const int pid = a.ids[t];                                                                            \
-        const PairHdr h = a.pairs[pid];                                                                      \
+        const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;                                \
+        if (t >= (long long)a.n * a.items) return;                                                           \
+        const int pid = a.ids[t / a.items];                                                                  \
+        const int item = (int)(t % a.items);                                                                 \
+        PairHdr h = a.pairs[pid];                                                                            \
+        if (item > h.nprim) return;                                                                          \
         const PrimPair<double>* pr = (const PrimPair<double>*)a.prims64;                                     \
-        double qm = 0.0;                                                                                     \
-        quartet_##NAME<double, 1>(h, h, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm, 0.0f, 0, true);             \
-        a.Q[pid] = sqrt(qm);                                                                                 \
-        for (int k = 0; k < h.nprim; k++) { /* bound of each primitive pair alone */                         \
-            PairHdr h1 = h;                                                                                  \
-            h1.prim0 = h.prim0 + k;                                                                          \
-            h1.nprim = 1;                                                                                    \
-            double qk = 0.0;                                                                                 \
-            quartet_##NAME<double, 1>(h1, h1, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qk, 0.0f, 0, true);       \
-            a.Bprim[h.prim0 + k] = sqrt(qk);                                                                 \
+        if (item > 0) { /* bound of one primitive pair alone */                                              \
+            h.prim0 += item - 1;                                                                             \
+            h.nprim = 1;                                                                                     \
         }                                                                                                    \
+        double qm = 0.0;                                                                                     \
+        quartet_##NAME<double, 1>(h, h, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm, 0.0f, 0, true); \
+        if (item == 0)                                                                                       \
+            a.Q[pid] = sqrt(qm);                                                                             \
+        else                                                                                                 \
+            a.Bprim[h.prim0] = sqrt(qm);                                                                     \
     }                                                                                                        \
     void launch_schwarz_##NAME(const SchwarzArgs& a, int block, cudaStream_t s)                             \
     {                                                                                                        \
-        if (a.n > 0) k_schwarz_##NAME<<<(a.n + block - 1) / block, block, 0, s>>>(a);                        \
+        const long long items = (long long)a.n * a.items;                                                    \
+        if (items > 0) k_schwarz_##NAME<<<(unsigned)((items + block - 1) / block), block, 0, s>>>(a);        \
     }
 
 // Batched build: one persistent kernel per class over many molecules.  Warps

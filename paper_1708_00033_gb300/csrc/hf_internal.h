@@ -61,6 +61,7 @@ struct SchwarzArgs {
     double* Q;            // [pair id] output bound
     const double* boys64;
     double* Bprim;        // [primitive pair] output bound of each primitive pair
+    int items;            // threads per pair: 1 + the largest primitive-pair count
 };
 
 // One molecule's view of one class in a batched build.

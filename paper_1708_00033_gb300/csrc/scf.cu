@@ -274,6 +274,7 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
     }
     int since_full = 0;
     bool force_full = true;
+    bool inc_on = o.incremental != 0;  // cleared once the test passes on an incremental build
     std::vector<const double*> fptr(m_diis), eptr(m_diis);
     for (it = 1; it <= o.max_iter; it++) {
         double E_el = 0.0;
@@ -286,7 +287,7 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
             rc = hf_fock_build(S, P.as<double>(), Fslot, nullptr, nullptr, &E_el, nullptr, pflags);
             if (rc != HF_OK) return rc;
         } else {
-            full = force_full || since_full >= o.rebuild_every;
+            full = !inc_on || force_full || since_full >= o.rebuild_every;
             if (full) {  // J, K of the full density
                 rc = hf_fock_build_partial(S, P.as<double>(), 0, 1, Jacc.as<double>(), Kacc.as<double>(), pflags);
                 if (rc != HF_OK) return rc;
@@ -358,7 +359,9 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
                 converged = 1;
                 break;
             }
-            force_full = true;  // confirm on a build from the full density
+            // the accumulated J, K carry the screening error of every difference build since the last
+            // full one: finish with builds from the full density, as the plain method would
+            inc_on = false;
         }
         if (mixed && it > 1 && fabs(E - E_old) < o.mixed_switch) {
             mixed = false;  // switch to FP64-only builds; the mixed-phase Fock matrices leave the DIIS history

@@ -183,16 +183,19 @@ def test_shards_sum_to_full_build(ctx, oracle_mod, n_shards):
     assert np.abs(F - full["F"]).max() <= 1e-12
 
 
-@pytest.mark.parametrize("eps", [1e-3, 1e-6])
-def test_density_screened_difference_build(ctx, oracle_mod, eps):
+@pytest.mark.parametrize("eps,prim_tau", [(1e-3, 0.0), (1e-6, 0.0), (1e-6, 1e-14)])
+def test_density_screened_difference_build(ctx, oracle_mod, eps, prim_tau):
     """J and K of a density change dP built with the density-weighted test
     (a quartet is skipped when 4 Q_ab Q_cd max|dP| over the six blocks it
-    touches is below the Schwarz threshold) against the oracle's Schwarz-only
+    touches is below the Schwarz threshold; its primitive quartets are
+    screened against prim_tau / max|dP|) against the oracle's Schwarz-only
     build of dP.  A skipped quartet changes a J element by less than tau and a
-    K element by less than tau/2, and at most 2 n_pairs quartets touch a J
-    element and 4 n_sh^2 a K element: that is the tolerance."""
+    K element by less than tau/2, a skipped primitive quartet by less than
+    4 prim_tau (at most 81 per quartet here), and at most 2 n_pairs quartets
+    touch a J element and 4 n_sh^2 a K element: that is the tolerance."""
     from paper_1708_00033_gb300 import hf
     tau = 1e-10
+    per_quartet = tau + 81 * 4 * prim_tau
     geom = I.water_cluster(4, I.CONFIG_SINGLE_BUILD)
     basis = I.synthetic_basis(geom)
     mol = oracle_mod.Molecule(geom, basis)
@@ -203,15 +206,16 @@ def test_density_screened_difference_build(ctx, oracle_mod, eps):
     P1 = oracle_mod.density_from_orbitals(oracle_mod.orthonormalise(C1, S))
     dP = P1 - P0
     J_ref, K_ref = mol.jk_unique(dP, tau)
-    s = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=0.0)
+    s = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=prim_tau)
     J, K = hf.fock_build_partial(s, dP, density_screen=True, fp64_only=True)
     n_sh = basis.n_shells
     n_pairs = n_sh * (n_sh + 1) // 2
-    assert np.abs(J - J_ref).max() <= 2 * n_pairs * tau
-    assert np.abs(K - K_ref).max() <= 4 * n_sh * n_sh * 0.5 * tau
-    # and the same call without the density test is the plain Schwarz-screened build
-    J2, K2 = hf.fock_build_partial(s, dP, fp64_only=True)
-    assert np.abs(J2 - J_ref).max() <= 1e-12 and np.abs(K2 - K_ref).max() <= 1e-12
+    assert np.abs(J - J_ref).max() <= 2 * n_pairs * per_quartet
+    assert np.abs(K - K_ref).max() <= 4 * n_sh * n_sh * per_quartet
+    if prim_tau == 0.0:
+        # the same call without the density test is the plain Schwarz-screened build
+        J2, K2 = hf.fock_build_partial(s, dP, fp64_only=True)
+        assert np.abs(J2 - J_ref).max() <= 1e-12 and np.abs(K2 - K_ref).max() <= 1e-12
 
 
 @pytest.mark.parametrize("copies", [2, 152, 608])
