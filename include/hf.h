@@ -251,11 +251,13 @@ int hf_fock_build_partial(hf_system* sys, const double* P, int shard, int n_shar
  *              builds, so the final energy is that of the plain FP64 method.
  *   incremental  1: between full rebuilds, J and K are updated with the J and
  *              K of P_k - P_ref (hf_fock_build_partial with HF_DENSITY_SCREEN),
- *              so small density changes skip most quartets.  Once the
- *              convergence test passes on such a build, every further build
- *              is a full one and convergence is only declared on a full build
- *              (so the final energy is that of the plain method).
- *   rebuild_every  full rebuild period of the incremental mode (0: 8). */
+ *              so small density changes skip most quartets.  Once |dE| falls
+ *              below incremental_switch (or the convergence test passes on such
+ *              a build), every further build is a full one, the DIIS history
+ *              restarts, and convergence is only declared on a full build (so
+ *              the final energy is that of the plain method).
+ *   rebuild_every  full rebuild period of the incremental mode (0: 8).
+ *   incremental_switch  |dE| below which incremental builds stop (0: 1e-5). */
 typedef struct {
     int32_t n_occ;
     int32_t max_iter;
@@ -266,6 +268,7 @@ typedef struct {
     double mixed_switch;
     int32_t incremental;
     int32_t rebuild_every;
+    double incremental_switch;
 } hf_scf_opts;
 
 /* Result of hf_scf_run. */

@@ -36,6 +36,14 @@ __device__ __forceinline__ void comp_pow(int l, int c, int& x, int& y, int& z)
     x = y = z = 0;
 }
 
+// position of the exponent triple e = (x, y, z), |e| = t <= 4, in a packed list ordered by |e|,
+// then by x descending, then by y descending (35 entries for |e| <= 4)
+__device__ __forceinline__ int eidx(int x, int y, int z)
+{
+    const int t = x + y + z, r = t - x;
+    return t * (t + 1) * (t + 2) / 6 + r * (r + 1) / 2 + z;
+}
+
 __device__ __forceinline__ double binom(int n, int k)
 {
     return (n == 2 && k == 1) ? 2.0 : 1.0;  // n <= 2
@@ -97,19 +105,20 @@ __global__ void k_one_electron(int n_sh, int n_atoms, int N, const int* __restri
                             s[d][u][v] = PB[d] * s[d][u][v - 1] + o2p * (v - 1) * (v >= 2 ? s[d][u][v - 2] : 0.0);
                     }
             }
-            // nuclear-attraction auxiliaries, e up to Lab (<= 4), m up to Lab
-            double V[36];  // (a|b) for this primitive pair, summed over nuclei
-            for (int c = 0; c < 36; c++) V[c] = 0.0;
-            const double K = exp(-mu * ((A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) +
-                                        (A[2] - B[2]) * (A[2] - B[2])));
+            // nuclear-attraction auxiliaries [e|0]^(m), e up to Lab (<= 4), m up to Lab; their m = 0
+            // level, weighted by the nuclear charges, is summed over the nuclei first, and the
+            // binomial shift to (a|b) (linear in [e|0]) is applied once per primitive pair
+            double ts[35];  // sum over nuclei of Z_C [e|0]^(0), packed by eidx
+            for (int c = 0; c < 35; c++) ts[c] = 0.0;
+            const double K = exp(-mu * R2ab);
+            const double pre = 2.0 * M_PI / p * K;
             for (int nuc = 0; nuc < n_atoms; nuc++) {
                 const double PC[3] = {P[0] - xyz[3 * nuc], P[1] - xyz[3 * nuc + 1], P[2] - xyz[3 * nuc + 2]};
                 double F[5];
                 boys_eval<4>(p * (PC[0] * PC[0] + PC[1] * PC[1] + PC[2] * PC[2]), boys64, F);
-                // th[m][x][y][z], x+y+z <= Lab - m
-                double th[5][5][5][5];
-                const double pre = 2.0 * M_PI / p * K;
-                for (int m = 0; m <= Lab; m++) th[m][0][0][0] = pre * F[m];
+                // th[m][eidx(e)], |e| <= Lab - m
+                double th[5][35];
+                for (int m = 0; m <= Lab; m++) th[m][0] = pre * F[m];
                 for (int tot = 1; tot <= Lab; tot++)
                     for (int m = 0; m <= Lab - tot; m++)
                         for (int x = tot; x >= 0; x--)
@@ -119,31 +128,43 @@ __global__ void k_one_electron(int n_sh, int n_atoms, int N, const int* __restri
                                 const int d = x > 0 ? 0 : (y > 0 ? 1 : 2);
                                 int e1[3] = {x, y, z};
                                 e1[d]--;
-                                double v = PA[d] * th[m][e1[0]][e1[1]][e1[2]] - PC[d] * th[m + 1][e1[0]][e1[1]][e1[2]];
+                                const int i1 = eidx(e1[0], e1[1], e1[2]);
+                                double v = PA[d] * th[m][i1] - PC[d] * th[m + 1][i1];
                                 if (e1[d] > 0) {
                                     int e2[3] = {e1[0], e1[1], e1[2]};
                                     e2[d]--;
-                                    v += e1[d] * o2p * (th[m][e2[0]][e2[1]][e2[2]] - th[m + 1][e2[0]][e2[1]][e2[2]]);
+                                    const int i2 = eidx(e2[0], e2[1], e2[2]);
+                                    v += e1[d] * o2p * (th[m][i2] - th[m + 1][i2]);
                                 }
-                                th[m][e[0]][e[1]][e[2]] = v;
+                                th[m][eidx(e[0], e[1], e[2])] = v;
                             }
-                for (int ca = 0; ca < na; ca++) {
-                    int ax, ay, az;
-                    comp_pow(la, ca, ax, ay, az);
-                    for (int cb = 0; cb < nb; cb++) {
-                        int bx, by, bz;
-                        comp_pow(lb, cb, bx, by, bz);
-                        double acc = 0.0;
-                        for (int kx = 0; kx <= bx; kx++)
-                            for (int ky = 0; ky <= by; ky++)
-                                for (int kz = 0; kz <= bz; kz++) {
-                                    const double w = binom(bx, kx) * binom(by, ky) * binom(bz, kz) *
-                                                     pow(A[0] - B[0], bx - kx) * pow(A[1] - B[1], by - ky) *
-                                                     pow(A[2] - B[2], bz - kz);
-                                    acc += w * th[0][ax + kx][ay + ky][az + kz];
-                                }
-                        V[ca * nb + cb] -= Z[nuc] * acc;
-                    }
+                const double zc = Z[nuc];
+                const int ne = (Lab + 1) * (Lab + 2) * (Lab + 3) / 6;
+                for (int c = 0; c < ne; c++) ts[c] += zc * th[0][c];
+            }
+            // (a|b) = sum_k C(b,k) (A-B)^(b-k) [a+k|0] per direction
+            double ABp[3][3];
+            for (int d = 0; d < 3; d++) {
+                ABp[d][0] = 1.0;
+                ABp[d][1] = A[d] - B[d];
+                ABp[d][2] = ABp[d][1] * ABp[d][1];
+            }
+            double V[36];  // (a|b) for this primitive pair, summed over nuclei
+            for (int ca = 0; ca < na; ca++) {
+                int ax, ay, az;
+                comp_pow(la, ca, ax, ay, az);
+                for (int cb = 0; cb < nb; cb++) {
+                    int bx, by, bz;
+                    comp_pow(lb, cb, bx, by, bz);
+                    double acc = 0.0;
+                    for (int kx = 0; kx <= bx; kx++)
+                        for (int ky = 0; ky <= by; ky++)
+                            for (int kz = 0; kz <= bz; kz++) {
+                                const double w = binom(bx, kx) * binom(by, ky) * binom(bz, kz) * ABp[0][bx - kx] *
+                                                 ABp[1][by - ky] * ABp[2][bz - kz];
+                                acc += w * ts[eidx(ax + kx, ay + ky, az + kz)];
+                            }
+                    V[ca * nb + cb] = -acc;
                 }
             }
             for (int ca = 0; ca < na; ca++) {

@@ -131,8 +131,10 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
         if (o.diis_off) o.diis_size = 0;
         if (o.mixed_switch == 0.0) o.mixed_switch = 1e-5;
         if (o.rebuild_every <= 0) o.rebuild_every = 8;
+        if (o.incremental_switch == 0.0) o.incremental_switch = 1e-5;
     }
     if (!opts_in) o.rebuild_every = 8;
+    if (!opts_in) o.incremental_switch = 1e-5;
     if (!opts_in) o.mixed_switch = 1e-5;
     bool mixed = S->th.fp32_cutoff > 0.0;
     const int N = S->n_bf;
@@ -274,7 +276,7 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
     }
     int since_full = 0;
     bool force_full = true;
-    bool inc_on = o.incremental != 0;  // cleared once the test passes on an incremental build
+    bool inc_on = o.incremental != 0;  // cleared near convergence: the rest are full builds
     std::vector<const double*> fptr(m_diis), eptr(m_diis);
     for (it = 1; it <= o.max_iter; it++) {
         double E_el = 0.0;
@@ -362,6 +364,13 @@ extern "C" int hf_scf_run(hf_system* S, const hf_scf_opts* opts_in, const double
             // the accumulated J, K carry the screening error of every difference build since the last
             // full one: finish with builds from the full density, as the plain method would
             inc_on = false;
+        }
+        if (inc_on && it > 1 && fabs(E - E_old) < o.incremental_switch) {
+            // near convergence the difference builds' accumulated screening error (a Fock matrix that
+            // depends on the path, not only on P) would stall DIIS: full builds from here on, and the
+            // Fock matrices of the incremental phase leave the DIIS history
+            inc_on = false;
+            nh = 0;
         }
         if (mixed && it > 1 && fabs(E - E_old) < o.mixed_switch) {
             mixed = false;  // switch to FP64-only builds; the mixed-phase Fock matrices leave the DIIS history

@@ -87,7 +87,8 @@ class Peaks_c(ctypes.Structure):
 class ScfOpts_c(ctypes.Structure):
     _fields_ = [("n_occ", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("e_tol", ctypes.c_double),
                 ("d_tol", ctypes.c_double), ("diis_size", ctypes.c_int32), ("diis_off", ctypes.c_int32),
-                ("mixed_switch", ctypes.c_double), ("incremental", ctypes.c_int32), ("rebuild_every", ctypes.c_int32)]
+                ("mixed_switch", ctypes.c_double), ("incremental", ctypes.c_int32), ("rebuild_every", ctypes.c_int32),
+                ("incremental_switch", ctypes.c_double)]
 
 
 class ScfResult_c(ctypes.Structure):
@@ -462,11 +463,11 @@ def guess_predict(model: Model, system: "System") -> np.ndarray:
 
 def scf(system: "System", n_occ: int = 0, max_iter: int = 100, e_tol: float = 1e-9, d_tol: float = 1e-6,
         diis_size: int = 8, P_guess=None, raise_on_noconv: bool = True, mixed_switch: float = 1e-5,
-        incremental: bool = False, rebuild_every: int = 8) -> dict:
+        incremental: bool = False, rebuild_every: int = 8, incremental_switch: float = 1e-5) -> dict:
     """hf_scf_run with host arrays; returns energy, density, orbital energies and timings."""
     N = system.n_bf
     o = ScfOpts_c(int(n_occ), int(max_iter), float(e_tol), float(d_tol), int(diis_size), 1 if diis_size == 0 else 0,
-                  float(mixed_switch), 1 if incremental else 0, int(rebuild_every))
+                  float(mixed_switch), 1 if incremental else 0, int(rebuild_every), float(incremental_switch))
     P_out = np.empty((N, N))
     eps = np.zeros(N)
     en = np.zeros(max_iter)
