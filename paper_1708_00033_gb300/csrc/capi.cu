@@ -440,6 +440,19 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
         S->plan[ci].n64 = totals_h[2 * ci];
         S->plan[ci].n32 = totals_h[2 * ci + 1];
     }
+    // bra lookup tables (their sizes follow from the quartet totals)
+    for (int ci = 0; ci < kNumClasses; ci++) {
+        auto& pl = S->plan[ci];
+        const int nb = S->class_count[kEriClasses[ci].X];
+        if (pl.n64 > 0) {
+            TRY(pl.chunk64.alloc(sizeof(int) * chunk_entries(pl.n64)));
+            KCHK(launch_chunk_bra(nb, pl.offsets64.as<long long>(), pl.n64, pl.chunk64.as<int>(), st));
+        }
+        if (pl.n32 > 0) {
+            TRY(pl.chunk32.alloc(sizeof(int) * chunk_entries(pl.n32)));
+            KCHK(launch_chunk_bra(nb, pl.offsets32.as<long long>(), pl.n32, pl.chunk32.as<int>(), st));
+        }
+    }
     HF_CUDA(cudaGetLastError());
     return HF_OK;
 }
@@ -537,7 +550,8 @@ int hf_system_get_info(const hf_system* S, hf_system_info* info)
     for (auto* b : bufs) bytes += b->bytes;
     for (int c = 0; c < kNumPairClasses; c++) bytes += S->class_ids[c].bytes + S->class_q[c].bytes;
     for (int c = 0; c < kNumClasses; c++)
-        bytes += S->plan[c].offsets64.bytes + S->plan[c].offsets32.bytes + S->plan[c].kstart32.bytes;
+        bytes += S->plan[c].offsets64.bytes + S->plan[c].offsets32.bytes + S->plan[c].kstart32.bytes +
+                 S->plan[c].chunk64.bytes + S->plan[c].chunk32.bytes;
     info->device_bytes = bytes;
     return HF_OK;
 }
@@ -665,6 +679,7 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
             if (n > 0) {
                 a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
                 a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
+                a.chunk = prec ? pl.chunk32.as<int>() : pl.chunk64.as<int>();
                 a.n_quartets = n;
                 const int use_f32 = prec && !(flags & HF_FP64_ONLY);
                 // a class too small to fill the GPU with one thread per quartet shares each quartet's
@@ -788,6 +803,7 @@ int hf_fock_build_partial(hf_system* S, const double* P, int shard, int n_shards
             if (q1 <= q0) continue;
             a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
             a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
+            a.chunk = prec ? pl.chunk32.as<int>() : pl.chunk64.as<int>();
             a.q_begin = q0;
             a.n_quartets = q1;
             const int use_f32 = prec && !(flags & HF_FP64_ONLY);

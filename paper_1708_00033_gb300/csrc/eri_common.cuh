@@ -143,6 +143,19 @@ __device__ __forceinline__ int find_bra(const long long* __restrict__ off, int n
     return lo;
 }
 
+// Largest b in [lo, hi] with off[b] <= q, given off[lo] <= q (the bra lookup tables bound the range).
+__device__ __forceinline__ int find_bra_in(const long long* __restrict__ off, int lo, int hi, long long q)
+{
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= q)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 constexpr int kEriThreads = 128;
 
 // Density-weighted screening: a quartet (AB|CD) changes the six Fock blocks of Eq. 1a-1f by at most
@@ -187,7 +200,9 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
             PairHdr hb, hk;                                                                                  \
             double f = 1.0;                                                                                  \
             if (valid) {                                                                                     \
-                const int b = find_bra(a.offsets, a.n_bra, q);                                               \
+                const long long c = q >> kChunkShift;                                                        \
+                const int b = a.chunk ? find_bra_in(a.offsets, a.chunk[c], a.chunk[c + 1], q)                 \
+                                      : find_bra(a.offsets, a.n_bra, q);                                     \
                 const int k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                        \
                 hb = a.pairs[a.bra[b]];                                                                      \
                 hk = a.pairs[a.ket[k]];                                                                      \

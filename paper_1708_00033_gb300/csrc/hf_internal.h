@@ -14,6 +14,7 @@ namespace hf {
 constexpr int kMaxL = 2;
 constexpr int kNumPairClasses = 6;  // ss ps pp ds dp dd
 constexpr int kNumClasses = 21;     // (X|Y), X >= Y
+constexpr int kChunkShift = 10;      // quartets per entry of the bra lookup tables: 1024
 constexpr int kMaxPrim = 8;         // primitives per shell accepted by the library
 
 // One significant shell pair, oriented so that l_A >= l_B.
@@ -49,6 +50,8 @@ struct EriArgs {
     const float* dsh;                 // [n_sh x n_sh] max |P| per shell block (nullptr: no density screening)
     int n_sh;
     float dtau;                       // density-weighted screening threshold
+    const int* chunk;                 // [c] bra of quartet min(c << kChunkShift, n_quartets_all - 1)
+                                      // (nullptr: each quartet's bra by binary search over all bras)
     int n_copies;                     // > 1: block b accumulates into copy b % n_copies of Jt / Kt
     long long copy_stride;            // doubles between copies
 };
@@ -174,6 +177,7 @@ struct hf_system {
     // quartet schedule per class
     struct ClassPlan {
         hf::DevBuf offsets64, offsets32, kstart32;
+        hf::DevBuf chunk64, chunk32;  // bra of every 2^kChunkShift-th quartet (see EriArgs::chunk)
         long long n64 = 0, n32 = 0;
         long long n_unscreened = 0;
     } plan[hf::kNumClasses];

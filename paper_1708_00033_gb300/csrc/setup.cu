@@ -534,4 +534,24 @@ int launch_scan(int n, const long long* in, long long* out, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Bra lookup table of one class and precision: entry c = bra of quartet min(c << kChunkShift, n - 1),
+// c = 0 .. ((n - 1) >> kChunkShift) + 1, so that quartet q's bra lies in [t[q >> S], t[(q >> S) + 1]].
+__global__ void k_chunk_bra(int n_bra, const long long* __restrict__ off, long long n, long long n_entries,
+                            int* __restrict__ out)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_entries) return;
+    const long long q = min(c << kChunkShift, n - 1);
+    out[c] = find_bra(off, n_bra, q);
+}
+
+long long chunk_entries(long long n) { return n > 0 ? ((n - 1) >> kChunkShift) + 2 : 0; }
+
+int launch_chunk_bra(int n_bra, const long long* off, long long n, int* out, cudaStream_t s)
+{
+    const long long e = chunk_entries(n);
+    if (e > 0) k_chunk_bra<<<(unsigned)((e + 255) / 256), 256, 0, s>>>(n_bra, off, n, e, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace hf

@@ -38,6 +38,8 @@ int launch_one_electron(int n_sh, int n_atoms, int N, const int* l, const int* a
 int launch_nuclear_repulsion(int n_atoms, const double* xyz, const double* Z, double* out, cudaStream_t s);
 
 // Fock assembly
+long long chunk_entries(long long n);
+int launch_chunk_bra(int n_bra, const long long* off, long long n, int* out, cudaStream_t s);
 int launch_sum_copies(int n_copies, long long nn, const double* in, double* out, int num_sms, cudaStream_t s);
 int launch_axpby(long long n, const double* A, double alpha, const double* B, double* C, cudaStream_t s);
 int launch_shell_block_max(int n_sh, int N, const int* l, const int* bf0, const double* P, float* dsh, cudaStream_t s);
