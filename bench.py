@@ -28,6 +28,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 DFMA_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal, derived)
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant kernel, from one
+# ncu capture of the default workload, with the SHA-256 of the sources that kernel is compiled from at that
+# time; the bench reports it only while those sources are unchanged (else the counters describe another
+# kernel and traffic is null).
+NCU_TRAFFIC = {"kernel": "k_eri_1000", "bytes_per_launch": None, "sources_sha256": None}
+TRAFFIC_SOURCES = ("paper_1708_00033_gb300/csrc/gen_eri.py", "paper_1708_00033_gb300/csrc/eri_common.cuh",
+                   "paper_1708_00033_gb300/csrc/hf_internal.h")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(root, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str):
+    if NCU_TRAFFIC["kernel"] != kernel or NCU_TRAFFIC["bytes_per_launch"] is None:
+        return None
+    return NCU_TRAFFIC["bytes_per_launch"] if kernel_sources_sha256() == NCU_TRAFFIC["sources_sha256"] else None
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -243,7 +267,8 @@ def run_ours(a):
         "clocks": clk,
         "roofline": {"bound": "alu", "kernel": hf.CLASS_KERNELS[c], "class": hf.CLASS_NAMES[c], "achieved": achieved,
                      "peak": DFMA_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / DFMA_PEAK_GFLOPS,
-                     "traffic": None, "peak_kind": "FP64 FMA pipe, derived from unit counts and max clock",
+                     "traffic": measured_traffic(hf.CLASS_KERNELS[c]),
+                     "peak_kind": "FP64 FMA pipe, derived from unit counts and max clock (hf_measure_peaks: 1,252)",
                      "all_eri_kernels": {"ms": eri_ms, "achieved": eri_gflops,
                                          "frac": eri_gflops / DFMA_PEAK_GFLOPS}},
         "class_ms": {hf.CLASS_NAMES[i]: round(float(ms_cls[i]), 3) for i in range(len(ms_cls))},
