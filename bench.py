@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--prim-tau", type=float, default=1e-14)
+    ap.add_argument("--reference-seconds", type=float, default=150.0,
+                    help="oracle time budget of --impl reference over all its steps")
     ap.add_argument("--mode", default="fock", choices=["fock", "scf", "mixed", "batch", "guess", "copies", "peaks"])
     ap.add_argument("--n-train", type=int, default=2000)
     ap.add_argument("--n-eval", type=int, default=32)
@@ -327,7 +329,7 @@ def run_reference(a):
     mol = oracle.Molecule(geom, basis)
     S, _ = mol.core_hamiltonian()
     P = random_density(S, inputs.n_electrons(geom) // 2, a.config_id, 0)
-    per_step = max(2.0, 150.0 / max(1, a.steps + a.warmup))
+    per_step = max(1.0, a.reference_seconds / max(1, a.steps + a.warmup))
     for w in range(a.warmup):
         _oracle_sample(a, geom, basis, P, per_step / 4, offset=w, mol=mol)
     est = []
