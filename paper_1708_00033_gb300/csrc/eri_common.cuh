@@ -15,11 +15,8 @@
 
 namespace hf {
 
-// 16-byte aligned (80 B for double, 48 B for float) so that a lane's loads of one record
-// become 16-byte vector loads: the ket records of a warp's lanes are scattered, and the
-// number of L1 sector accesses, not the bytes, limits those loads.
 template <typename real>
-struct __align__(16) PrimPair {
+struct PrimPair {
     real p;              // a + b
     real Px, Py, Pz;     // (a A + b B) / p
     real PAx, PAy, PAz;  // P - A
