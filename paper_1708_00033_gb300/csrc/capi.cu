@@ -569,6 +569,15 @@ int hf_one_electron(hf_system* S, double* Sout, double* Hout, int flags)
     return HF_OK;
 }
 
+// Floats per lane of the FP32 kernels' shared-memory ket staging: one ket's primitive-pair records,
+// rounded up to an odd count; 0 (global reads) if a block's staging would exceed 48 KB.
+static int fp32_stage_stride(const hf_system& X)
+{
+    int per = X.maxpp * (int)(sizeof(PrimPair<float>) / sizeof(float));
+    per |= 1;
+    return stage_bytes(per, kEriThreads) <= 48 * 1024 ? per : 0;
+}
+
 // Accumulators of one build: the system's Jt / Kt (one copy shared by every block, updated with FP64
 // atomics), or fock_copies zeroed copies of each, block b writing copy b % fock_copies, summed into
 // Jt / Kt after the ERI launches (the GPU analogue of the paper's private Fock matrices).
@@ -682,6 +691,7 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
                 a.chunk = prec ? pl.chunk32.as<int>() : pl.chunk64.as<int>();
                 a.n_quartets = n;
                 const int use_f32 = prec && !(flags & HF_FP64_ONLY);
+                a.stage_stride = use_f32 ? fp32_stage_stride(X) : 0;
                 // a class too small to fill the GPU with one thread per quartet shares each quartet's
                 // primitive work among a lane group instead (shorter latency, same result)
                 const int lanes = (!use_f32 && n < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
@@ -807,6 +817,7 @@ int hf_fock_build_partial(hf_system* S, const double* P, int shard, int n_shards
             a.q_begin = q0;
             a.n_quartets = q1;
             const int use_f32 = prec && !(flags & HF_FP64_ONLY);
+            a.stage_stride = use_f32 ? fp32_stage_stride(X) : 0;
             const int lanes = (!use_f32 && q1 - q0 < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
             const long long blocks = ((q1 - q0) * lanes + kEriThreads - 1) / kEriThreads;
             const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);

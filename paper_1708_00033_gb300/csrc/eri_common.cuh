@@ -158,6 +158,16 @@ __device__ __forceinline__ int find_bra_in(const long long* __restrict__ off, in
 
 constexpr int kEriThreads = 128;
 
+// Shared-memory staging of the ket primitive records in the FP32 ERI kernels.  A warp's 32 lanes
+// work on 32 different kets, so each lane's loads of its ket records in the primitive loop hit 32
+// different L1 sectors per instruction; the FP32 kernels were bound by that L1 throughput.  The warp
+// instead copies the 32 kets' record blocks with coalesced loads into 32 slots of stride
+// a.stage_stride floats (odd, so equal offsets in different slots fall in different banks) and the
+// primitive loop reads them from shared memory.
+extern __shared__ float kstage_smem[];
+
+inline size_t stage_bytes(int stage_stride, int block) { return (size_t)block * (size_t)stage_stride * sizeof(float); }
+
 // Density-weighted screening: a quartet (AB|CD) changes the six Fock blocks of Eq. 1a-1f by at most
 // Q_AB Q_CD times the largest |P| of the blocks (CD), (AB), (BD), (AC), (BC), (AD) it is contracted with
 // (times 4 for the Coulomb weight); density_block_max returns that largest |P|.  The quartet is skipped
@@ -219,7 +229,25 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
                 live = valid && 4.0f * (float)(hb.Q * hk.Q) * dm >= a.dtau;                                  \
                 pt = ptau / fmaxf(dm, 1e-30f);                                                               \
             }                                                                                                \
-            nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane, live); \
+            const PrimPair<real>* kst = nullptr;                                                            \
+            if constexpr (sizeof(real) == 4) {                                                               \
+                if (a.stage_stride > 0) { /* warp-uniform: copy the 32 lanes' ket records */                 \
+                    float* wsm = kstage_smem + (size_t)(threadIdx.x >> 5) * 32 * a.stage_stride;             \
+                    const int wl = threadIdx.x & 31;                                                         \
+                    __syncwarp();                                                                            \
+                    for (int j = 0; j < 32; j++) {                                                           \
+                        const int p0 = __shfl_sync(0xffffffffu, hk.prim0, j);                                \
+                        const int nf = __shfl_sync(0xffffffffu, hk.nprim, j) * (int)(sizeof(PrimPair<float>) / 4); \
+                        const float* src = (const float*)(prims + p0);                                       \
+                        float* dst = wsm + j * a.stage_stride;                                               \
+                        for (int t = wl; t < nf; t += 32) dst[t] = __ldg(src + t);                           \
+                    }                                                                                        \
+                    __syncwarp();                                                                            \
+                    kst = (const PrimPair<real>*)(wsm + wl * a.stage_stride);                                \
+                }                                                                                            \
+            }                                                                                                \
+            nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane, live,  \
+                                               kst);                                                         \
         }                                                                                                    \
         if (a.prim_count) {                                                                                  \
             const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \
@@ -229,7 +257,7 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
     void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s, int lanes)   \
     {                                                                                                        \
         if (use_f32)                                                                                         \
-            k_eri_##NAME<float, 1><<<grid, block, 0, s>>>(a);                                                \
+            k_eri_##NAME<float, 1><<<grid, block, stage_bytes(a.stage_stride, block), s>>>(a);              \
         else if (lanes > 1)                                                                                  \
             k_eri_##NAME<double, (GL)><<<grid, block, 0, s>>>(a);                                            \
         else                                                                                                 \

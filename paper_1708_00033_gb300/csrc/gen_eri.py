@@ -387,12 +387,13 @@ def gen_class(X, Y):
     out.append(f"__device__ __forceinline__ int quartet_{name}(const PairHdr& hb, const PairHdr& hk,"
                f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
     out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
-    out.append(f"    float ptau, int lane, bool valid)")
+    out.append(f"    float ptau, int lane, bool valid, const PrimPair<real>* kstage = nullptr)")
     out.append("{")
     out.append("    // surviving primitive quartets form a staircase (pairs sorted by bound): bra primitive ib")
-    out.append("    // pairs with the first nk(ib) ket primitives, nk non-increasing; one flat loop over it")
+    out.append("    // pairs with the first nk(ib) ket primitives, nk non-increasing; one flat loop over it.")
+    out.append("    // kstage: the ket's records staged in shared memory by the caller (nullptr: read them globally)")
     out.append("    const PrimPair<real>* __restrict__ bpp = prims + hb.prim0;")
-    out.append("    const PrimPair<real>* __restrict__ kpp = prims + hk.prim0;")
+    out.append("    const PrimPair<real>* __restrict__ kpp = kstage ? kstage : prims + hk.prim0;")
     out.append("    const int nbp = hb.nprim;")
     out.append("    int nkb = hk.nprim;")
     out.append("    int total = 0;")

@@ -52,6 +52,8 @@ struct EriArgs {
     float dtau;                       // density-weighted screening threshold
     const int* chunk;                 // [c] bra of quartet min(c << kChunkShift, n_quartets_all - 1)
                                       // (nullptr: each quartet's bra by binary search over all bras)
+    int stage_stride;                 // FP32 launches: floats per lane of the shared-memory ket staging
+                                      // (0: ket records read from global memory)
     int n_copies;                     // > 1: block b accumulates into copy b % n_copies of Jt / Kt
     long long copy_stride;            // doubles between copies
 };
