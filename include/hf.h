@@ -366,9 +366,9 @@ int hf_batch_tune(hf_batch* batch, const char* cache_path, int64_t sample_quarte
 
 /* A small MLP that predicts density-matrix blocks from atom-pair geometry, as
  * an SCF starting point.  The paper has no counterpart (its SCF starts from
- * the core Hamiltonian, Section 3); the plain SCF is the fallback and the
- * judge of the result, so a guess changes iteration counts, never the
- * converged energy.
+ * the core Hamiltonian, Section 3); the plain SCF is the fallback, and the
+ * SCF iterations started from the guess decide the result, so a guess changes
+ * iteration counts, never the converged energy.
  *   features (16 per unordered atom pair a <= b): R, u = (r_b - r_a)/R (3),
  *     u_i u_j (9), one-hot element pair (O-O, O-H, H-H); for O-H the O atom
  *     is first; on-site pairs have R = 0 and u = 0.
