@@ -39,3 +39,30 @@ def test_no_device_is_reported_not_crashed():
     rc = lib.hf_create(ctypes.byref(h), 0, None)
     assert rc in (hf.HF_E_UNSUPPORTED, hf.HF_E_CUDA, hf.HF_E_INVALID)
     assert not h.value
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: without the built CUDA library the binding raises."""
+    from paper_1708_00033_gb300 import hf
+    monkeypatch.setattr(hf, "_lib", None)
+    monkeypatch.setattr(hf, "LIB_PATH", os.path.join(os.path.dirname(hf.LIB_PATH), "does-not-exist.so"))
+    with pytest.raises(RuntimeError):
+        hf.load_library()
+
+
+def test_product_does_not_use_the_oracle():
+    """The package (binding, drivers, CUDA sources) never imports or links the oracle."""
+    import re
+    import paper_1708_00033_gb300 as pkg
+    root = os.path.dirname(pkg.__file__)
+    pat = re.compile(r"^\s*(import\s+oracle|from\s+oracle|#include\s+[\"<].*oracle)", re.M)
+    hits = []
+    for d, _, files in os.walk(root):
+        if "_build" in d or "__pycache__" in d:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                with open(os.path.join(d, f)) as fh:
+                    if pat.search(fh.read()):
+                        hits.append(f)
+    assert not hits, hits
