@@ -84,14 +84,6 @@ int fail(int code, const std::string& msg)
         if ((x) != 0) return cuda_status(cudaGetLastError(), "kernel launch " #x); \
     } while (0)
 
-template <typename T>
-int upload(DevBuf& b, const T* host, size_t n, cudaStream_t s)
-{
-    TRY(b.alloc(n * sizeof(T)));
-    if (n) HF_CUDA(cudaMemcpyAsync(b.p, host, n * sizeof(T), cudaMemcpyHostToDevice, s));
-    return HF_OK;
-}
-
 size_t next_pow2(size_t n)
 {
     size_t p = 1;

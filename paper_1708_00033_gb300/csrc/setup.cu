@@ -300,46 +300,6 @@ int launch_sort_prims(long long n_pairs, const PairHdr* pairs, const double* Bpr
 }
 
 // ------------------------------------------------------- quartet schedule --
-// For bra b of class X: kets of class Y (sorted by Q descending) with
-// Q_b Q_k >= tau form a prefix; when X == Y only kets k <= b are unique.
-// The prefix splits into an FP64 head (Q_b Q_k >= cutoff) and an FP32 tail.
-__global__ void k_ket_counts(int n_bra, const double* __restrict__ qb, int n_ket, const double* __restrict__ qk,
-                             int same, double tau, double cutoff, long long* __restrict__ c64,
-                             long long* __restrict__ c32, int* __restrict__ kstart32)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_bra) return;
-    const double Qb = qb[b];
-    int n = n_ket;
-    if (tau > 0.0) {
-        int lo = 0, hi = n_ket;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (Qb * qk[mid] >= tau)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        n = lo;
-    }
-    if (same && n > b + 1) n = b + 1;
-    int n64 = n;
-    if (cutoff > 0.0) {
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (Qb * qk[mid] >= cutoff)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        n64 = lo;
-    }
-    c64[b] = n64;
-    c32[b] = n - n64;
-    kstart32[b] = n64;
-}
-
 // exclusive scan of n counts into out[0..n] (single block, chunked)
 __global__ void k_scan(int n, const long long* __restrict__ in, long long* __restrict__ out)
 {
@@ -411,7 +371,10 @@ int launch_sig_scatter(long long n_pairs, long long n_seg, const int* pclass, co
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// k_ket_counts with the list lengths read on the device (entries b >= n_bra get zero counts)
+// For bra b of class X: kets of class Y (sorted by Q descending) with Q_b Q_k >= tau form a
+// prefix; when X == Y only kets k <= b are unique.  The prefix splits into an FP64 head
+// (Q_b Q_k >= cutoff) and an FP32 tail.  The list lengths are read on the device (entries
+// b >= n_bra get zero counts), so the schedule needs no host round trip.
 __global__ void k_ket_counts_dev(int cap, const unsigned* __restrict__ n_bra_p, const double* __restrict__ qb,
                                  const unsigned* __restrict__ n_ket_p, const double* __restrict__ qk, int same,
                                  double tau, double cutoff, long long* __restrict__ c64, long long* __restrict__ c32,
@@ -517,14 +480,6 @@ int launch_class_scatter_sig(long long n, const int* pclass, const double* Q, in
 {
     if (n > 0)
         k_class_scatter_sig<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, pclass, Q, X, qmax, tau, cursor, key, val);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
-int launch_ket_counts(int n_bra, const double* qb, int n_ket, const double* qk, int same, double tau, double cutoff,
-                      long long* c64, long long* c32, int* kstart32, cudaStream_t s)
-{
-    if (n_bra > 0)
-        k_ket_counts<<<(n_bra + 255) / 256, 256, 0, s>>>(n_bra, qb, n_ket, qk, same, tau, cutoff, c64, c32, kstart32);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

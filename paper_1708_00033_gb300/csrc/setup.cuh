@@ -20,8 +20,6 @@ int launch_class_scatter_sig(long long n, const int* pclass, const double* Q, in
                              unsigned* cursor, double* key, int* val, cudaStream_t s);
 int bitonic_sort_desc(double* key, int* val, int n, int n_pad, cudaStream_t s);
 int launch_sort_prims(long long n_pairs, const PairHdr* pairs, const double* Bprim, void* p64, void* p32, cudaStream_t s);
-int launch_ket_counts(int n_bra, const double* qb, int n_ket, const double* qk, int same, double tau, double cutoff,
-                      long long* c64, long long* c32, int* kstart32, cudaStream_t s);
 int launch_scan(int n, const long long* in, long long* out, cudaStream_t s);
 int launch_sig_scatter(long long n_pairs, long long n_seg, const int* pclass, const double* Q,
                        const unsigned long long* qmax_bits, double tau, const size_t* seg_host, unsigned* cursor,
