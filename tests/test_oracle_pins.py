@@ -316,3 +316,22 @@ def test_literal_vs_unique_four_waters(oracle_mod):
     Ju, Ku = m.jk_unique(P)
     Jl, Kl = m.jk_literal(P)
     assert np.abs(Ju - Jl).max() < 1e-11 and np.abs(Ku - Kl).max() < 1e-11
+
+
+@pytest.mark.parametrize("tau", [0.0, 1e-10])
+def test_strided_sample_partitions_the_unique_loop(oracle_mod, dimer, tau):
+    """The CPU-baseline sample (every stride-th bra pair) partitions Algorithm 1's
+    unique-quartet loop: over all offsets the evaluated quartets add up to the full
+    loop's count and the spanned quartets to n_p (n_p + 1) / 2."""
+    n_sh = dimer.n_shells
+    n_p = n_sh * (n_sh + 1) // 2
+    S, _ = dimer.core_hamiltonian()
+    P = oracle_mod.density_from_orbitals(oracle_mod.orthonormalise(I.random_orbitals(dimer.n_bf, 10, 1, 0), S))
+    dimer.jk_unique(P, tau)
+    full = dimer.last_quartets
+    stride = 7
+    got = [dimer.jk_unique_sample(P, tau, stride, off) for off in range(stride)]
+    assert sum(n for n, _ in got) == full
+    assert sum(u for _, u in got) == n_p * (n_p + 1) // 2
+    if tau == 0.0:
+        assert full == n_p * (n_p + 1) // 2
