@@ -527,4 +527,8 @@ def main(outdir):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else os.path.join(os.path.dirname(os.path.abspath(__file__)), "generated"))
+    import argparse
+    ap = argparse.ArgumentParser(description="Generate the per-class ERI kernels and their table.")
+    ap.add_argument("out", nargs="?", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "generated"),
+                    help="output directory (default: the package's csrc/generated)")
+    main(ap.parse_args().out)
