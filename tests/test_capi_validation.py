@@ -100,3 +100,36 @@ def test_malformed_input_is_rejected(case, code):
     rc, msg = _create(Z, xyz, atom, l, nprim, exps, coefs, th)
     assert rc == code, msg
     assert msg
+
+
+def test_null_handles_are_rejected():
+    """Every entry point answers a NULL handle with HF_E_INVALID (destroy: a no-op), on CPU."""
+    lib = hf.load_library()
+    n = None
+    buf = np.zeros(16)
+    p = buf.ctypes.data
+    calls = {
+        "hf_fock_build": lambda: lib.hf_fock_build(n, p, p, n, n, None, None, 0),
+        "hf_fock_build_partial": lambda: lib.hf_fock_build_partial(n, p, 0, 1, p, p, 0),
+        "hf_scf_run": lambda: lib.hf_scf_run(n, None, n, n, n, None, None, 0),
+        "hf_eigh": lambda: lib.hf_eigh(n, 2, p, p, p, 0),
+        "hf_system_set_fock_copies": lambda: lib.hf_system_set_fock_copies(n, 1),
+        "hf_measure_peaks": lambda: lib.hf_measure_peaks(n, None),
+        "hf_one_electron": lambda: lib.hf_one_electron(n, p, p, 0),
+        "hf_system_get_info": lambda: lib.hf_system_get_info(n, None),
+        "hf_fock_build_noalloc": lambda: lib.hf_fock_build_noalloc(n, p, p, n, n),
+        "hf_fock_build_batch": lambda: lib.hf_fock_build_batch(n, p, p, None, None, 0),
+        "hf_batch_tune": lambda: lib.hf_batch_tune(n, None, 0),
+        "hf_batch_get_info": lambda: lib.hf_batch_get_info(n, None),
+        "hf_batch_offsets": lambda: lib.hf_batch_offsets(n, None),
+        "hf_model_create": lambda: lib.hf_model_create(n, n, None),
+        "hf_model_get_weights": lambda: lib.hf_model_get_weights(n, n, n),
+        "hf_model_forward": lambda: lib.hf_model_forward(n, 1, p, p, 0),
+        "hf_model_train_step": lambda: lib.hf_model_train_step(n, 1, p, p, p, 1e-3, None, 0),
+        "hf_guess_features": lambda: lib.hf_guess_features(n, n, n, None, 0),
+        "hf_guess_predict": lambda: lib.hf_guess_predict(n, n, n, 0),
+    }
+    for name, call in calls.items():
+        assert call() == hf.HF_E_INVALID, name
+    for name in ("hf_destroy", "hf_system_destroy", "hf_batch_destroy", "hf_model_destroy"):
+        getattr(lib, name)(None)
