@@ -10,8 +10,12 @@ collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the CPU oracle (as it stands) on the host cores over
-strided samples of the same Fock build and reports the same metric.
+The default line also carries the SCF half of the metric (plain FP64, mixed
+precision, and mixed precision from the learned guess on held-out 32-water
+clusters), the roofline of the dominant ERI kernel, and the CPU oracle's
+baseline.  --impl reference times the CPU oracle (as it stands) on the host
+cores over stratified random samples of the same Fock build and reports the
+same metric.  --mode shard shards one molecule's build over the ranks.
 """
 from __future__ import annotations
 
@@ -68,10 +72,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
-    ap.add_argument("--prim-tau", type=float, default=1e-14)
+    ap.add_argument("--prim-tau", type=float, default=None, help="default: the benchmark primitive threshold")
     ap.add_argument("--reference-seconds", type=float, default=150.0,
                     help="oracle time budget of --impl reference over all its steps")
-    ap.add_argument("--mode", default="fock", choices=["fock", "scf", "mixed", "batch", "guess", "copies", "peaks"])
+    ap.add_argument("--mode", default="fock",
+                    choices=["fock", "scf", "mixed", "batch", "guess", "copies", "peaks", "shard"])
     ap.add_argument("--n-train", type=int, default=2000)
     ap.add_argument("--n-eval", type=int, default=32)
     ap.add_argument("--train-steps", type=int, default=4000)
@@ -79,7 +84,13 @@ def parse():
     ap.add_argument("--scf-variants", default="fp64,mixed,fp64_incremental,mixed_incremental")
     ap.add_argument("--copies", default="1,8,152,608", help="accumulator copies compared by --mode copies")
     ap.add_argument("--copies-workloads", default="4:0,16:1e-10,64:1e-10", help="waters:schwarz_tau list")
+    ap.add_argument("--scf-clusters", type=int, default=4,
+                    help="held-out 32-water clusters of the SCF comparison in the default line (0: none)")
+    ap.add_argument("--scf-waters", type=int, default=32)
     a = ap.parse_args()
+    if a.prim_tau is None:
+        from paper_1708_00033_gb300 import inputs
+        a.prim_tau = inputs.BENCH_PRIM_TAU
     if a.mode == "mixed" and "--waters" not in sys.argv:
         a.waters, a.config_id = 256, 3
     if a.mode == "mixed" and "--fp32-cutoff" not in sys.argv:
@@ -277,51 +288,177 @@ def run_ours(a):
     }
     if e2e:
         line["e2e"] = e2e
+    if a.scf_clusters > 0:
+        line["scf"] = scf_comparison(a, ctx, hf, inputs, rank)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a, geom, basis, P, a.cpu_sample_seconds)
+        line["cpu_baseline"] = cpu_baseline(a, geom, basis, P, a.cpu_sample_seconds, hf=hf, ctx=ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def _oracle_sample(a, geom, basis, P, seconds, offset=0, mol=None):
-    """Time the oracle on every stride-th bra pair; extrapolate to one build."""
-    import oracle
-    if mol is None:
-        mol = oracle.Molecule(geom, basis)
-    mol.schwarz()  # setup, untimed
-    n_sh = mol.n_shells
-    n_p = n_sh * (n_sh + 1) // 2
-    total_unscreened = n_p * (n_p + 1) // 2
-    # calibrate the stride on a tiny sample
-    stride = max(1, n_p // 8)
-    t0 = time.perf_counter()
-    _, u0 = mol.jk_unique_sample(P, a.tau, stride, offset)
-    dt0 = max(time.perf_counter() - t0, 1e-3)
-    rate = u0 / dt0
-    stride = max(1, int(stride * (dt0 / seconds)) if dt0 < seconds else stride)
-    t0 = time.perf_counter()
-    nq, u = mol.jk_unique_sample(P, a.tau, stride, offset)
-    dt = time.perf_counter() - t0
-    build_s = dt * total_unscreened / max(u, 1)
-    return mol, {"seconds": dt, "stride": stride, "quartets": nq, "unscreened_rows": u,
-                 "est_build_s": build_s, "value": 1.0 / build_s, "rate_hint": rate}
+def screened_row_counts(Qp, tau: float, block: int = 8192):
+    """Exact number of quartets Algorithm 1 evaluates in each row ij (kets kl <= ij with Q_ij Q_kl >= tau),
+    from the pair bounds Qp in canonical pair order; blocked so that memory stays O(block^2)."""
+    import numpy as np
+    n = Qp.size
+    if tau <= 0:
+        return np.arange(1, n + 1, dtype=np.int64)
+    counts = np.empty(n, dtype=np.int64)
+    for b0 in range(0, n, block):
+        b1 = min(n, b0 + block)
+        thr = tau / np.maximum(Qp[b0:b1], 1e-300)
+        prefix = np.sort(Qp[:b0])
+        c = prefix.size - np.searchsorted(prefix, thr, side="left")
+        M = np.tril(Qp[b0:b1][None, :] >= thr[:, None])
+        counts[b0:b1] = c + M.sum(axis=1)
+    return counts
 
 
-def cpu_baseline(a, geom, basis, P, seconds):
+class OracleEstimator:
+    """Time of one full oracle Fock build of a large system, estimated from timed random samples of rows
+    (bra pairs ij of Algorithm 1's outer loop).  Rows are stratified by the bra's pair class (ss, ps, pp,
+    ds, dp, dd); within a class the sampled rows' work is scaled by the ratio of the class's exact screened
+    quartet count (from the Schwarz bounds) to the sampled rows' count.  The work of a row is the time a
+    thread spends in it (the oracle sums it over its threads), so that a sample too small to keep every
+    thread busy still measures its rows; the full build's wall time is that work divided by the thread
+    count and by the parallel efficiency the oracle reaches on a full build of a small system
+    (calibrate())."""
+
+    def __init__(self, mol, P, tau):
+        import numpy as np
+        import oracle
+        self.mol, self.P, self.tau = mol, P, tau
+        self.threads = oracle.num_threads()
+        self.efficiency = 1.0
+        Q = mol.schwarz()
+        n = mol.n_shells
+        i, j = np.tril_indices(n)  # canonical order: ij = i (i + 1) / 2 + j, j <= i
+        order = np.lexsort((j, i))
+        i, j = i[order], j[order]
+        self.Qp = Q[i, j]
+        lsh = np.asarray([0 if c == 1 else (1 if c == 3 else 2) for c in mol.ncomp])
+        la, lb = np.maximum(lsh[i], lsh[j]), np.minimum(lsh[i], lsh[j])
+        self.cls = np.array([{(0, 0): 0, (1, 0): 1, (1, 1): 2, (2, 0): 3, (2, 1): 4, (2, 2): 5}[(a, b)]
+                             for a, b in zip(la, lb)])
+        self.counts = screened_row_counts(self.Qp, tau)
+        self.total = int(self.counts.sum())
+        self.strata = [c for c in range(6) if self.counts[self.cls == c].sum() > 0]
+
+    def calibrate(self, mol, P, tau):
+        """Parallel efficiency of a full build of a small system: (thread-seconds / threads) / wall seconds."""
+        import numpy as np
+        rows = np.arange(mol.n_shells * (mol.n_shells + 1) // 2)
+        t0 = time.perf_counter()
+        _, busy = mol.jk_unique_rows(P, tau, rows)
+        wall = time.perf_counter() - t0
+        self.efficiency = min(1.0, busy / self.threads / wall)
+        return {"wall_s": wall, "thread_s": busy, "efficiency": self.efficiency}
+
+    def estimate(self, seconds: float, rng):
+        """One estimate of the full build's wall seconds from about `seconds` of sampled rows' work."""
+        import numpy as np
+        per = seconds / len(self.strata)
+        work, sampled = 0.0, 0
+        for c in self.strata:
+            rows = np.flatnonzero((self.cls == c) & (self.counts > 0))
+            perm = rng.permutation(rows)
+            # pilot: a few rows give this class's work per quartet, then the rest of its budget
+            k, acc = 0, 0
+            while k < perm.size and acc < 2000:
+                acc += int(self.counts[perm[k]])
+                k += 1
+            _, w_pilot = self.mol.jk_unique_rows(self.P, self.tau, perm[:k])
+            rate = acc / max(w_pilot, 1e-6)
+            want = int(rate * max(per - w_pilot, 0.0))
+            k2, acc2 = k, 0
+            while k2 < perm.size and acc2 < want:
+                acc2 += int(self.counts[perm[k2]])
+                k2 += 1
+            w_main = self.mol.jk_unique_rows(self.P, self.tau, perm[k:k2])[1] if k2 > k else 0.0
+            q_s = acc + acc2
+            work += (w_pilot + w_main) * (int(self.counts[rows].sum()) / q_s)
+            sampled += q_s
+        return work / (self.threads * self.efficiency), sampled
+
+
+def _time_oracle_full(mol, P, tau):
+    t0 = time.perf_counter()
+    mol.jk_unique(P, tau)
+    return time.perf_counter() - t0, mol.last_quartets
+
+
+def _gpu_build_ms(hf, ctx, geom, basis, P, tau, prim_tau, reps=3):
+    import torch
+    s = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=prim_tau)
+    Pd = torch.from_numpy(P).cuda()
+    F = torch.empty_like(Pd)
+    s.fock_build(Pd, F=F)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.fock_build(Pd, F=F)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    s.close()
+    return min(ms)
+
+
+def cpu_baseline(a, geom, basis, P, seconds, hf=None, ctx=None):
+    """The oracle on the host cores: a stratified-sample estimate of one build of the benchmarked workload
+    (the line's value), and full, unextrapolated builds of the 4-water cluster (100 BF, no screening) and of
+    the first 16 waters of the 256-water cluster (400 BF, Schwarz 1e-10), each beside the GPU's time for
+    the same build."""
+    import numpy as np
     import oracle
-    _, r = _oracle_sample(a, geom, basis, P, seconds)
-    return {"value": r["value"], "unit": "Fock builds/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"oracle unique-quartet digestion over every {r['stride']}-th bra shell pair "
-                       f"({r['quartets']} screened quartets, {r['seconds']:.1f} s), scaled by the unscreened "
-                       f"quartets the sampled rows span to one full build ({r['est_build_s']:.0f} s)")}
+    from paper_1708_00033_gb300 import inputs
+    mol = oracle.Molecule(geom, basis)
+    t0 = time.perf_counter()
+    est = OracleEstimator(mol, P, a.tau)
+    setup_s = time.perf_counter() - t0
+    calib = est.calibrate(*_calibration_system(inputs))
+    build_s, q = est.estimate(seconds, np.random.default_rng(12345))
+    full = {}
+    for name, g, tau, cfg in (("C1_4_waters_tau0", inputs.water_cluster(4, inputs.CONFIG_SINGLE_BUILD), 0.0, 1),
+                              ("subset_16_waters_tau1e-10",
+                               inputs.subset_waters(inputs.water_cluster(256, inputs.CONFIG_MIXED), 16), 1e-10, 3)):
+        b = inputs.synthetic_basis(g)
+        m = oracle.Molecule(g, b)
+        S, _ = m.core_hamiltonian()
+        Pm = random_density(S, inputs.n_electrons(g) // 2, cfg, 0)
+        if tau > 0:
+            m.schwarz()
+        osec, nq = _time_oracle_full(m, Pm, tau)
+        row = {"n_bf": m.n_bf, "schwarz_tau": tau, "oracle_s": osec, "oracle_quartets": nq}
+        if hf is not None:
+            gms = _gpu_build_ms(hf, ctx, g, b, Pm, tau, a.prim_tau)
+            row.update(gpu_ms=gms, gpu_over_oracle=osec / (gms / 1e3))
+        full[name] = row
+    return {"value": 1.0 / build_s, "unit": "Fock builds/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"stratified random sample of bra-pair rows (6 pair classes, {q} of {est.total} screened "
+                       f"quartets, ~{seconds:.0f} s), each class scaled by its exact screened quartet count: "
+                       f"{build_s:.0f} s per build"),
+            "estimate_s_per_build": build_s, "setup_s": setup_s, "calibration": calib, "full_builds": full}
+
+
+def _calibration_system(inputs):
+    """The 4-water cluster without screening: the full build whose parallel efficiency calibrates the
+    sampled estimates."""
+    import oracle
+    g = inputs.water_cluster(4, inputs.CONFIG_SINGLE_BUILD)
+    m = oracle.Molecule(g, inputs.synthetic_basis(g))
+    S, _ = m.core_hamiltonian()
+    return m, random_density(S, inputs.n_electrons(g) // 2, 1, 0), 0.0
 
 
 def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import numpy as np
     import oracle
     from paper_1708_00033_gb300 import inputs
     geom = inputs.water_cluster(a.waters, a.config_id, 0)
@@ -329,23 +466,142 @@ def run_reference(a):
     mol = oracle.Molecule(geom, basis)
     S, _ = mol.core_hamiltonian()
     P = random_density(S, inputs.n_electrons(geom) // 2, a.config_id, 0)
+    est = OracleEstimator(mol, P, a.tau)
+    calib = est.calibrate(*_calibration_system(inputs))
     per_step = max(1.0, a.reference_seconds / max(1, a.steps + a.warmup))
-    for w in range(a.warmup):
-        _oracle_sample(a, geom, basis, P, per_step / 4, offset=w, mol=mol)
-    est = []
-    for k in range(a.steps):
-        _, r = _oracle_sample(a, geom, basis, P, per_step, offset=a.warmup + k, mol=mol)
-        est.append(r)
-    build_s = sum(r["est_build_s"] for r in est) / len(est)
+    rng = np.random.default_rng(777)
+    for _ in range(a.warmup):
+        est.estimate(per_step, rng)
+    runs = [est.estimate(per_step, rng)[0] for _ in range(a.steps)]
+    build_s = float(np.mean(runs))
+    spread = float(np.std(runs, ddof=1)) if len(runs) > 1 else 0.0
     value = 1.0 / build_s
     line = {"metric": "Fock builds/s", "value": value, "unit": "Fock builds/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": build_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": workload_name(a), "waters": a.waters, "schwarz_tau": a.tau},
             "cpu_baseline": {"value": value, "unit": "Fock builds/s", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"{a.steps} strided bra-pair samples of ~{per_step:.0f} s each, scaled to one build"},
+                             "sample": (f"{a.steps} independent stratified random samples of bra-pair rows "
+                                        f"(~{per_step:.0f} s each), each scaled to one build by the exact screened "
+                                        f"quartet counts: {build_s:.0f} +- {spread:.0f} s per build")},
+            "estimate_spread_s": spread, "estimates_s": [round(x, 1) for x in runs], "calibration": calib,
             "e2e": {"value": value, "unit": "Fock builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def scf_comparison(a, ctx, hf, inputs, rank=0):
+    """The SCF half of the metric: time to a converged energy (|dE| < 1e-9, RMS dP < 1e-6; the energy then
+    agrees with the plain FP64 SCF's to 1e-8 Eh) on held-out 32-water clusters (seeds (6, m), never trained
+    on), for three arms: plain FP64 builds from the core-Hamiltonian guess; mixed precision (FP32 for
+    Q_ij Q_kl < 1e-4 until |dE| < 1e-5, then FP64) from the core guess; and mixed precision from the learned
+    guess of the shipped network.  Wall times of the SCF call (plus the prediction for the learned arm);
+    system setup is reported separately.  Each rank takes its own clusters."""
+    import numpy as np
+    import torch
+    from paper_1708_00033_gb300 import guess
+    w, meta = guess.load_weights()
+    model = hf.Model(ctx, w)
+    rows = []
+    for m in range(a.scf_clusters):
+        idx = rank * a.scf_clusters + m
+        geom = inputs.water_cluster(a.scf_waters, inputs.CONFIG_GUESS_EVAL, idx)
+        basis = inputs.synthetic_basis(geom)
+        row = {"cluster": idx}
+        for arm, cut, learned in (("fp64", 0.0, False), ("mixed", 1e-4, False), ("mixed_learned", 1e-4, True)):
+            t0 = time.perf_counter()
+            s = hf.System(ctx, geom, basis, schwarz_tau=a.tau, prim_tau=a.prim_tau, fp32_cutoff=cut)
+            torch.cuda.synchronize()
+            setup = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            Pg = guess.predict_or_none(model, s) if learned else None
+            r = hf.scf(s, e_tol=1e-9, d_tol=1e-6, P_guess=Pg, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            s.close()
+            row[arm] = {"s": dt, "iterations": r["iterations"], "mixed_iterations": r["mixed_iterations"],
+                        "converged": bool(r["converged"]), "energy": r["energy"], "setup_s": setup,
+                        "fock_s": r["seconds_fock"], "diag_s": r["seconds_diag"],
+                        "fallback_to_core": bool(learned and Pg is None)}
+            print(f"scf cluster {idx} {arm}: {r['iterations']} it {dt:.2f} s E={r['energy']:.10f}", file=sys.stderr,
+                  flush=True)
+        for arm in ("mixed", "mixed_learned"):
+            row[arm]["abs_dE_vs_fp64"] = abs(row[arm]["energy"] - row["fp64"]["energy"])
+        rows.append(row)
+    mean = lambda arm, k: float(np.mean([r[arm][k] for r in rows]))  # noqa: E731
+    out = {"metric": "SCF time to converged energy (|dE|<1e-9, RMS dP<1e-6)", "unit": "s",
+           "workload": f"{len(rows)} held-out {a.scf_waters}-water clusters (seeds (6, m)), "
+                       f"{25 * a.scf_waters} BF, Schwarz tau={a.tau:g}, primitive tau={a.prim_tau:g}",
+           "guess_network": meta,
+           "mean_s": {arm: mean(arm, "s") for arm in ("fp64", "mixed", "mixed_learned")},
+           "mean_iterations": {arm: mean(arm, "iterations") for arm in ("fp64", "mixed", "mixed_learned")},
+           "max_abs_dE_vs_fp64": {arm: float(max(r[arm]["abs_dE_vs_fp64"] for r in rows))
+                                  for arm in ("mixed", "mixed_learned")},
+           "all_converged": all(r[arm]["converged"] for r in rows for arm in ("fp64", "mixed", "mixed_learned")),
+           "rows": rows}
+    out["speedup_vs_fp64"] = {arm: out["mean_s"]["fp64"] / out["mean_s"][arm] for arm in ("mixed", "mixed_learned")}
+    return out
+
+
+def run_shard(a):
+    """One molecule's Fock build sharded over the ranks (strong scaling): every rank builds the quartet
+    shard `rank` of every angular class (hf_fock_build_partial), J and K are summed over the ranks with one
+    NCCL allreduce each as device tensors (the paper's ddi_gsumf), and the library assembles F.  At N = 1
+    the line also reports the largest difference from hf_fock_build."""
+    import torch
+    import torch.distributed as dist
+    from paper_1708_00033_gb300 import hf, inputs
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    geom = inputs.water_cluster(a.waters, a.config_id, 0)
+    basis = inputs.synthetic_basis(geom)
+    ctx = hf.Context(local)
+    sysm = hf.System(ctx, geom, basis, schwarz_tau=a.tau, fp32_cutoff=a.fp32_cutoff, prim_tau=a.prim_tau)
+    S, _ = sysm.one_electron()
+    P = random_density(S, inputs.n_electrons(geom) // 2, a.config_id, 0)
+    Pd = torch.from_numpy(P).to(dev)
+
+    def allsum(t):
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return t
+
+    for _ in range(a.warmup):
+        hf.sharded_fock_build(sysm, Pd, rank, world, allsum)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        F, J, K, E = hf.sharded_fock_build(sysm, Pd, rank, world, allsum)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    if world > 1:
+        total_ms = reduce_max(total_ms, dist, dev)
+        dist.barrier()
+    line = {"metric": "Fock builds/s", "value": a.steps / (total_ms / 1e3), "unit": "Fock builds/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a) + ", sharded over the ranks (J, K allreduce)",
+                       "parallelism": f"quartet shards x{world}, NCCL allreduce of J and K"},
+            "clocks": clk, "E_elec": E}
+    if world == 1:
+        ref = sysm.fock_build(Pd)
+        line["max_abs_dF_vs_fock_build"] = float((F - ref["F"]).abs().max())
+        line["abs_dE_vs_fock_build"] = abs(E - ref["E_elec"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def _scf_run(hf, sysm, **kw):
@@ -506,7 +762,7 @@ def run_guess(a):
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": a.n_eval, "warmup": 0, "dtype": "bf16+f32 (MLP), f64 (SCF)",
             "data": "synthetic",
             "config": {"workload": f"train {a.n_train} clusters U{{2..8}} waters seeds (5,m); eval {a.n_eval} 32-water clusters seeds (6,m)",
-                       "schwarz_tau": 1e-10, "prim_tau": 1e-14, "train_steps": a.train_steps},
+                       "schwarz_tau": a.tau, "prim_tau": a.prim_tau, "train_steps": a.train_steps},
             "dataset_s": data["seconds"], "train_samples": int(data["X"].shape[0]), "train_s": train_s,
             "final_loss": float(np.mean(losses[-100:])), "initial_loss": float(np.mean(losses[:10])),
             "mean_core_iterations": ev["mean_core_iterations"], "mean_learned_iterations": ev["mean_learned_iterations"],
@@ -605,6 +861,8 @@ def main():
         run_copies(a)
     elif a.mode == "peaks":
         run_peaks(a)
+    elif a.mode == "shard":
+        run_shard(a)
     else:
         run_ours(a)
 

@@ -137,7 +137,10 @@ typedef struct {
 /* Create a context on CUDA device `device` that orders all work on
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
  * stream is borrowed and must outlive the context.  Builds the Boys-function
- * tables on the device.  Errors: HF_E_INVALID (ctx NULL),
+ * tables on the device and looks up the address of the fixed scratch of
+ * hf_fock_build_noalloc, which makes the driver reserve that array (about
+ * 7.3 MB per device, held until the process exits) here rather than in a
+ * later call.  Errors: HF_E_INVALID (ctx NULL),
  * HF_E_UNSUPPORTED (device is not compute capability 10.3), HF_E_CUDA. */
 int hf_create(hf_ctx** ctx, int device, void* cuda_stream);
 
@@ -183,7 +186,10 @@ int hf_one_electron(hf_system* sys, double* S, double* H, int flags);
  *   J, K   [N*N] outputs (may be NULL).
  *   E_elec host scalar output 1/2 sum P (H + F) (may be NULL).
  *   stats  host output (may be NULL); HF_TIMING adds device times.
- * flags: HF_PTR_DEVICE (P, F, J, K are device pointers), HF_TIMING.
+ * flags: HF_PTR_DEVICE (P, F, J, K are device pointers), HF_TIMING,
+ * HF_FP64_ONLY.  The density check runs on the device: the host waits once,
+ * after the whole build, and a rejected density leaves every output
+ * untouched.
  * Errors: HF_E_INVALID (NULL sys/P, P not finite or not symmetric),
  * HF_E_NOMEM, HF_E_CUDA. */
 int hf_fock_build(hf_system* sys, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
@@ -234,6 +240,19 @@ int hf_system_set_fock_copies(hf_system* sys, int32_t copies);
  * SCF builds).  Errors: HF_E_INVALID (bad shard, NULL pointer, P not finite
  * or not symmetric), HF_E_CUDA. */
 int hf_fock_build_partial(hf_system* sys, const double* P, int shard, int n_shards, double* J, double* K, int flags);
+
+/* Assembly of a sharded build (the step after the paper's ddi_gsumf in
+ * Algorithms 2/3): F = H + J - K/2 from J and K already summed over every
+ * shard of hf_fock_build_partial (for example by one allreduce of J and one
+ * of K), and E_elec = 1/2 sum P (H + F) when E_elec is not NULL.
+ *   P      [N*N] total density (required only with E_elec).
+ *   J, K   [N*N] summed Coulomb and exchange matrices.
+ *   F      [N*N] output.
+ *   E_elec host scalar output or NULL.
+ * flags: HF_PTR_DEVICE (P, J, K, F are device pointers).  Errors:
+ * HF_E_INVALID (NULL argument, E_elec without P, J or K not finite), HF_E_CUDA. */
+int hf_fock_assemble(hf_system* sys, const double* P, const double* J, const double* K, double* F, double* E_elec,
+                     int flags);
 
 /* ------------------------------------------------------------------- SCF */
 
@@ -415,6 +434,39 @@ int hf_model_train_step(hf_model* model, int n, const float* X, const float* T, 
  * atoms other than the supported O and H. */
 int hf_guess_features(hf_system* sys, float* X, int32_t* meta, int64_t* n_pairs, int flags);
 
+/* Training targets of a system from a density (for example the converged
+ * density of the plain SCF): for atom pair t of hf_guess_features,
+ * T[t][head block] = the pair's block of P (rows = first atom's functions)
+ * and mask[t][head block] = 1; every other output is 0 in both.
+ *   P     [N*N] density;  T, mask  [n_pairs * 325] float outputs.
+ * flags: HF_PTR_DEVICE for device P, T, mask.  Errors: HF_E_INVALID,
+ * HF_E_UNSUPPORTED (atoms other than O and H), HF_E_NOMEM, HF_E_CUDA. */
+int hf_guess_targets(hf_system* sys, const double* P, float* T, float* mask, int flags);
+
+/* Options of hf_guess_train (zero-initialise, then set what differs). */
+typedef struct {
+    int32_t steps; /* Adam steps (required, > 0) */
+    int32_t batch; /* samples per minibatch (0: 2048; at most n) */
+    float lr;      /* peak learning rate (0: 1e-3) */
+    int32_t pad;
+    uint64_t seed; /* minibatch draws */
+} hf_train_opts;
+
+/* Minibatch training of the model on a dataset resident in device memory:
+ * for step k = 0..steps-1, sample j of the minibatch is dataset row
+ * SplitMix64(seed, k * batch + j) mod n (SplitMix64's output function applied
+ * to seed + (i + 1) * 0x9E3779B97F4A7C15); the masked loss of
+ * hf_model_train_step, its gradients, and one Adam step with learning rate
+ * lr (1 + cos(pi k / steps)) / 2 (cosine decay).  The model's Adam state
+ * continues from earlier calls.
+ *   X [n * 16], T [n * 325], mask [n * 325]  device pointers (HF_PTR_DEVICE
+ *   required), for example features and hf_guess_targets of many systems.
+ *   losses  host array of `steps` minibatch losses, or NULL.
+ * Errors: HF_E_INVALID (NULL argument, n <= 0, bad options, host pointers),
+ * HF_E_NOMEM, HF_E_CUDA. */
+int hf_guess_train(hf_model* model, int64_t n, const float* X, const float* T, const float* mask,
+                   const hf_train_opts* opts, float* losses, int flags);
+
 /* Predicted total density P[N*N]: MLP blocks placed at (a, b) and (b, a),
  * on-site blocks symmetrised, scaled so that tr(PS) = N_e.  flags:
  * HF_PTR_DEVICE.  Errors: HF_E_INVALID if the prediction is not finite or
@@ -438,12 +490,14 @@ int hf_guess_predict(hf_model* model, hf_system* sys, double* P, int flags);
  * path and no energy or statistics output.  The call allocates nothing: its
  * scratch (density copy, J/K accumulators, status flag; about 7.3 MB) is one
  * fixed __device__ array per device, held until the process exits and shared
- * by every call on that device.  The accumulators are cleared at the start of
- * each call; calls whose device work overlaps race on the array.  The first
- * call on a device looks the array's address up once; make it before any
- * stream capture.  Errors: HF_E_INVALID (NULL sys/P/F, more than
- * HF_NOALLOC_MAX_BF basis functions, P not finite or not symmetric),
- * HF_E_CUDA. */
+ * by every call on that device.  hf_create already looked up its address
+ * (and so made the driver reserve it); a context created after a device
+ * reset looks it up again.  The accumulators are cleared at the start of
+ * each call; calls whose device work overlaps race on the array.  A system
+ * with fp32_cutoff > 0 evaluates its small quartets in FP32, as hf_fock_build
+ * does without HF_FP64_ONLY.  Errors: HF_E_INVALID (NULL sys/P/F, more than
+ * HF_NOALLOC_MAX_BF basis functions, P not finite or not symmetric; the
+ * outputs are then left untouched), HF_E_CUDA. */
 int hf_fock_build_noalloc(hf_system* sys, const double* P, double* F, double* J, double* K);
 
 #ifdef __cplusplus

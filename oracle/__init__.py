@@ -11,6 +11,7 @@ What each function follows:
   * ``jk_literal``     J and K by their definitions over all ordered indices;
   * ``jk_unique``      Algorithm 1's unique shell quartets + Eq. 1a-1f;
   * ``jk_elements``    single J/K elements by definition (large systems);
+  * ``jk_shell_blocks`` whole shell blocks of J/K by definition (large systems);
   * ``fock``           F = H + J - K/2, E = 1/2 tr P(H+F) + E_nn;
   * ``scf``            the SCF cycle of Section 3 (symmetric orthogonalisation,
                        core-Hamiltonian guess, diagonalise, new density, stop on
@@ -75,6 +76,10 @@ def _load():
     lib.or_jk_unique_sample.restype = ctypes.c_int64
     lib.or_jk_unique_sample.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, ctypes.c_int64, ctypes.c_int64, _dp, _dp, ctypes.POINTER(ctypes.c_int64)]
     lib.or_jk_elements.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, ctypes.c_int, _ip, _ip, _dp, _dp]
+    lib.or_jk_unique_rows.restype = ctypes.c_int64
+    lib.or_jk_unique_rows.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp]
+    lib.or_jk_shell_blocks.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, ctypes.c_int, _ip, _ip, _dp, _dp]
     lib.or_num_threads.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -225,6 +230,21 @@ class Molecule:
                                         int(offset), _d(J), _d(K), ctypes.byref(u))
         return int(n), int(u.value)
 
+    def jk_unique_rows(self, P: np.ndarray, tau: float, rows):
+        """Unique-quartet digestion over the given bra pairs ij (rows of Algorithm 1's outer loop); returns
+        (quartets evaluated, seconds the threads spent in the rows summed over threads).  J and K of the
+        partial sum are discarded."""
+        N = self.n_bf
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        J, K = np.zeros((N, N)), np.zeros((N, N))
+        Q = self.schwarz() if tau > 0 else np.zeros((1, 1))
+        r = np.ascontiguousarray(rows, dtype=np.int64)
+        busy = ctypes.c_double(0.0)
+        n = _load().or_jk_unique_rows(self._h, _d(P), float(tau), _d(np.ascontiguousarray(Q)), int(r.size),
+                                      r.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _d(J), _d(K),
+                                      ctypes.byref(busy))
+        return int(n), float(busy.value)
+
     def jk_elements(self, P: np.ndarray, pairs, tau: float = 0.0):
         P = np.ascontiguousarray(P, dtype=np.float64)
         mu = np.ascontiguousarray([p[0] for p in pairs], dtype=np.int32)
@@ -234,6 +254,24 @@ class Molecule:
         _load().or_jk_elements(self._h, _d(P), float(tau), _d(np.ascontiguousarray(Q)), len(pairs), _i(mu), _i(nu),
                                _d(Jel), _d(Kel))
         return Jel, Kel
+
+    def jk_shell_blocks(self, P: np.ndarray, blocks, tau: float = 0.0):
+        """Whole (I, J) shell blocks of J and K by definition (list of (ncomp_I x ncomp_J) arrays each)."""
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        Il = np.ascontiguousarray([b[0] for b in blocks], dtype=np.int32)
+        Jl = np.ascontiguousarray([b[1] for b in blocks], dtype=np.int32)
+        sizes = [int(self.ncomp[i]) * int(self.ncomp[j]) for i, j in blocks]
+        Jo, Ko = np.zeros(sum(sizes)), np.zeros(sum(sizes))
+        Q = self.schwarz() if tau > 0 else np.zeros((1, 1))
+        _load().or_jk_shell_blocks(self._h, _d(P), float(tau), _d(np.ascontiguousarray(Q)), len(blocks), _i(Il), _i(Jl),
+                                   _d(Jo), _d(Ko))
+        outJ, outK, o = [], [], 0
+        for (i, j), n in zip(blocks, sizes):
+            shp = (int(self.ncomp[i]), int(self.ncomp[j]))
+            outJ.append(Jo[o:o + n].reshape(shp))
+            outK.append(Ko[o:o + n].reshape(shp))
+            o += n
+        return outJ, outK
 
 
 def fock_from_jk(H, J, K):

@@ -28,6 +28,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -553,12 +554,39 @@ void or_jk_literal(int N, const double* eri, const double* P, double* J, double*
  * Thread-private accumulators, summed at the end (the private-Fock pattern
  * of Algorithm 2).  Returns the number of shell quartets evaluated.
  */
+/* Wall-clock seconds (OpenMP's timer when available). */
+static double wall_seconds(void)
+{
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return ts.tv_sec + 1e-9 * ts.tv_nsec;
+#endif
+}
+
 static int64_t jk_unique_impl(void* h, const double* P, double tau, const double* Qsh, int64_t stride,
-                              int64_t offset, double* J, double* K);
+                              int64_t offset, const int64_t* rows, int64_t n_rows, double* J, double* K,
+                              double* busy);
 
 int64_t or_jk_unique(void* h, const double* P, double tau, const double* Qsh, double* J, double* K)
 {
-    return jk_unique_impl(h, P, tau, Qsh, 1, 0, J, K);
+    return jk_unique_impl(h, P, tau, Qsh, 1, 0, NULL, 0, J, K, NULL);
+}
+
+/*
+ * The same digestion restricted to an explicit list of bra pairs ij (rows of
+ * Algorithm 1's outer loop, in any order; used to time a random sample of
+ * rows of a large system).  Returns the quartets evaluated; *busy (if not
+ * NULL) receives the seconds the threads spent in the rows, summed over
+ * threads, so that a sample too small to keep every thread busy still
+ * measures the work of its rows.
+ */
+int64_t or_jk_unique_rows(void* h, const double* P, double tau, const double* Qsh, int64_t n_rows, const int64_t* rows,
+                          double* J, double* K, double* busy)
+{
+    return jk_unique_impl(h, P, tau, Qsh, 1, 0, rows, n_rows, J, K, busy);
 }
 
 /*
@@ -574,24 +602,29 @@ int64_t or_jk_unique_sample(void* h, const double* P, double tau, const double* 
     int64_t np = (int64_t)c->n_shells * (c->n_shells + 1) / 2, u = 0;
     for (int64_t ij = offset; ij < np; ij += stride) u += ij + 1;
     *unscreened = u;
-    return jk_unique_impl(h, P, tau, Qsh, stride, offset, J, K);
+    return jk_unique_impl(h, P, tau, Qsh, stride, offset, NULL, 0, J, K, NULL);
 }
 
 static int64_t jk_unique_impl(void* h, const double* P, double tau, const double* Qsh, int64_t stride,
-                              int64_t offset, double* J, double* K)
+                              int64_t offset, const int64_t* rows, int64_t n_rows, double* J, double* K,
+                              double* busy)
 {
     or_ctx* c = (or_ctx*)h;
     int n = c->n_shells, N = c->n_bf;
     double* Jt = (double*)calloc((size_t)N * N, sizeof(double));
     double* Kt = (double*)calloc((size_t)N * N, sizeof(double));
     int64_t count = 0;
-#pragma omp parallel reduction(+ : count)
+    double busy_sum = 0.0;
+#pragma omp parallel reduction(+ : count, busy_sum)
     {
         double* Jp = (double*)calloc((size_t)N * N, sizeof(double));
         double* Kp = (double*)calloc((size_t)N * N, sizeof(double));
         double blk[OR_MAXCOMP * OR_MAXCOMP * OR_MAXCOMP * OR_MAXCOMP];
+        const int64_t n_iter = rows ? n_rows : ((int64_t)n * (n + 1) / 2 - offset + stride - 1) / stride;
 #pragma omp for schedule(dynamic, 1)
-        for (int64_t ij = offset; ij < (int64_t)n * (n + 1) / 2; ij += stride) {
+        for (int64_t it = 0; it < n_iter; it++) {
+            const int64_t ij = rows ? rows[it] : offset + it * stride;
+            const double t_row = busy ? wall_seconds() : 0.0;
             int i = (int)((sqrt(8.0 * ij + 1.0) - 1.0) / 2.0);
             while ((int64_t)i * (i + 1) / 2 > ij) i--;
             while ((int64_t)(i + 1) * (i + 2) / 2 <= ij) i++;
@@ -622,6 +655,7 @@ static int64_t jk_unique_impl(void* h, const double* P, double tau, const double
                                 }
                 }
             }
+            if (busy) busy_sum += wall_seconds() - t_row;
         }
 #pragma omp critical
         {
@@ -640,6 +674,7 @@ static int64_t jk_unique_impl(void* h, const double* P, double tau, const double
         }
     free(Jt);
     free(Kt);
+    if (busy) *busy = busy_sum;
     return count;
 }
 
@@ -687,6 +722,75 @@ void or_jk_elements(void* h, const double* P, double tau, const double* Qsh, int
         K_el[e] = ksum;
     }
     free(shell_of);
+}
+
+/*
+ * Whole shell blocks of J and K by definition: for each requested shell pair
+ * (I, J), every component pair (mu in I, nu in J) of
+ *   J_mu,nu = sum_{lam, sig} P_lam,sig (mu nu | lam sig)
+ *   K_mu,nu = sum_{lam, sig} P_lam,sig (mu lam | nu sig)
+ * summed over every ordered shell pair (k, l).  With tau > 0 an integral is
+ * left out when the Schwarz bound of its own quartet is strictly below tau:
+ * Q_IJ Q_kl for the Coulomb integrals, Q_Ik Q_Jl for the exchange ones.
+ * Block b is written row-major (ncomp(I) x ncomp(J)) at offset off[b] of
+ * J_out and K_out, off[b] = sum of the sizes of the blocks before it.
+ */
+void or_jk_shell_blocks(void* h, const double* P, double tau, const double* Qsh, int n_blk, const int* I_list,
+                        const int* J_list, double* J_out, double* K_out)
+{
+    or_ctx* c = (or_ctx*)h;
+    int n = c->n_shells, N = c->n_bf;
+    int64_t off = 0;
+    for (int e = 0; e < n_blk; e++) {
+        const int I = I_list[e], Jsh = J_list[e];
+        const or_shell *A = &c->sh[I], *B = &c->sh[Jsh];
+        const int na = A->ncomp, nb = B->ncomp;
+        double jacc[OR_MAXCOMP * OR_MAXCOMP] = {0}, kacc[OR_MAXCOMP * OR_MAXCOMP] = {0};
+#pragma omp parallel
+        {
+            double jl[OR_MAXCOMP * OR_MAXCOMP] = {0}, kl_[OR_MAXCOMP * OR_MAXCOMP] = {0};
+            double blk[OR_MAXCOMP * OR_MAXCOMP * OR_MAXCOMP * OR_MAXCOMP];
+#pragma omp for schedule(dynamic, 4)
+            for (int64_t kl = 0; kl < (int64_t)n * n; kl++) {
+                const int k = (int)(kl / n), l = (int)(kl % n);
+                const or_shell *C = &c->sh[k], *D = &c->sh[l];
+                if (!(tau > 0.0 && Qsh[I * n + Jsh] * Qsh[k * n + l] < tau)) {
+                    eri_block(A, B, C, D, blk); /* (a b | cc d) */
+                    for (int a = 0; a < na; a++)
+                        for (int b = 0; b < nb; b++) {
+                            double s = 0.0;
+                            for (int cc = 0; cc < C->ncomp; cc++)
+                                for (int d = 0; d < D->ncomp; d++)
+                                    s += P[(C->bf0 + cc) * N + D->bf0 + d]
+                                       * blk[((a * nb + b) * C->ncomp + cc) * D->ncomp + d];
+                            jl[a * nb + b] += s;
+                        }
+                }
+                if (!(tau > 0.0 && Qsh[I * n + k] * Qsh[Jsh * n + l] < tau)) {
+                    eri_block(A, C, B, D, blk); /* (a cc | b d) */
+                    for (int a = 0; a < na; a++)
+                        for (int b = 0; b < nb; b++) {
+                            double s = 0.0;
+                            for (int cc = 0; cc < C->ncomp; cc++)
+                                for (int d = 0; d < D->ncomp; d++)
+                                    s += P[(C->bf0 + cc) * N + D->bf0 + d]
+                                       * blk[((a * C->ncomp + cc) * nb + b) * D->ncomp + d];
+                            kl_[a * nb + b] += s;
+                        }
+                }
+            }
+#pragma omp critical
+            for (int t = 0; t < na * nb; t++) {
+                jacc[t] += jl[t];
+                kacc[t] += kl_[t];
+            }
+        }
+        for (int t = 0; t < na * nb; t++) {
+            J_out[off + t] = jacc[t];
+            K_out[off + t] = kacc[t];
+        }
+        off += na * nb;
+    }
 }
 
 int or_num_threads(void)

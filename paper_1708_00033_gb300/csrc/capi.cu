@@ -1,6 +1,7 @@
 // C-ABI entry points (include/hf.h): argument checks, device memory, and the
 // order of the setup and Fock-build kernels on the context's stream.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -161,6 +162,9 @@ int hf_create(hf_ctx** out, int device, void* cuda_stream)
                 rc = cuda_status(cudaGetLastError(), "hf_create: local memory reservation");
         cudaGetLastError();
     }
+    // the allocation-free build's fixed scratch: looking its address up loads its module now, so that
+    // the driver reserves that memory here and not inside an hf_fock_build_noalloc call
+    if (rc == HF_OK) rc = noalloc_scratch_address(&c->noalloc_scratch);
     if (rc == HF_OK) {
         for (auto& ev : c->ev) {
             if (cudaEventCreate(&ev) != cudaSuccess) {
@@ -432,6 +436,20 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
         S->plan[ci].n64 = totals_h[2 * ci];
         S->plan[ci].n32 = totals_h[2 * ci + 1];
     }
+    // ket tables (field-major copies of each class's records in class-list order)
+    for (int c = 0; c < kNumPairClasses; c++) {
+        const int n = S->class_count[c];
+        if (n <= 0) continue;
+        const long long stride = ((long long)n + 31) / 32 * 32;
+        S->ket_stride[c] = stride;
+        const size_t rows = (size_t)X.maxpp;
+        TRY(S->ket_tab[c].alloc(rows * stride * (9 * sizeof(double) + 9 * sizeof(float) + sizeof(float))));
+        double* t64 = S->ket_tab[c].as<double>();
+        float* t32 = (float*)(t64 + 9 * rows * stride);
+        float* tB = t32 + 9 * rows * stride;
+        KCHK(launch_ket_table(n, X.maxpp, stride, S->class_ids[c].as<int>(), S->pairs.as<PairHdr>(), S->prims64.p,
+                              S->prims32.p, t64, t32, tB, st));
+    }
     // bra lookup tables (their sizes follow from the quartet totals)
     for (int ci = 0; ci < kNumClasses; ci++) {
         auto& pl = S->plan[ci];
@@ -491,6 +509,10 @@ int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis
     DeviceGuard g(ctx->device);
     hf_system* S = new hf_system();
     S->ctx = ctx;
+    {
+        const char* lay = getenv("HF_KET_LAYOUT");
+        S->ket_soa = !(lay && strcmp(lay, "aos") == 0);
+    }
     S->device = ctx->device;
     S->stream = ctx->stream;
     if (th) S->th = *th;
@@ -540,7 +562,7 @@ int hf_system_get_info(const hf_system* S, hf_system_info* info)
                             &S->pair_class, &S->S, &S->H, &S->P64, &S->P32, &S->Jt, &S->Kt, &S->F, &S->Ebuf,
                             &S->Qall, &S->staging_P, &S->staging_out};
     for (auto* b : bufs) bytes += b->bytes;
-    for (int c = 0; c < kNumPairClasses; c++) bytes += S->class_ids[c].bytes + S->class_q[c].bytes;
+    for (int c = 0; c < kNumPairClasses; c++) bytes += S->class_ids[c].bytes + S->class_q[c].bytes + S->ket_tab[c].bytes;
     for (int c = 0; c < kNumClasses; c++)
         bytes += S->plan[c].offsets64.bytes + S->plan[c].offsets32.bytes + S->plan[c].kstart32.bytes +
                  S->plan[c].chunk64.bytes + S->plan[c].chunk32.bytes;
@@ -628,6 +650,69 @@ int hf_system_set_fock_copies(hf_system* S, int32_t copies)
     return HF_OK;
 }
 
+}  // extern "C"
+
+// The per-class ERI launches shared by hf_fock_build, hf_fock_build_partial and hf_fock_build_noalloc.
+int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int flags, cudaEvent_t* ev,
+                           unsigned long long* prim_count)
+{
+    hf_ctx* ctx = S->ctx;
+    cudaStream_t st = ctx->stream;
+    hf_system& X = *S;
+    a.pairs = S->pairs.as<PairHdr>();
+    a.prims64 = S->prims64.p;
+    a.prims32 = S->prims32.p;
+    a.N = S->n_bf;
+    a.boys64 = ctx->boys64.as<double>();
+    a.boys32 = ctx->boys32.as<float>();
+    a.prim_tau = S->th.prim_tau;
+    for (int ci = 0; ci < kNumClasses; ci++) {
+        const auto& pl = S->plan[ci];
+        const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
+        a.bra = S->class_ids[Xc].as<int>();
+        a.ket = S->class_ids[Yc].as<int>();
+        a.n_bra = S->class_count[Xc];
+        a.same = Xc == Yc;
+        for (int prec = 0; prec < 2; prec++) {
+            const long long n = prec ? pl.n32 : pl.n64;
+            const long long q0 = n * shard / n_shards, q1 = n * (shard + 1) / n_shards;
+            if (ev) HF_CUDA(cudaEventRecord(ev[4 * ci + 2 * prec], st));
+            a.prim_count = prim_count ? prim_count + 2 * ci + prec : nullptr;
+            if (q1 > q0) {
+                a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
+                a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
+                a.chunk = prec ? pl.chunk32.as<int>() : pl.chunk64.as<int>();
+                a.q_begin = q0;
+                a.n_quartets = q1;
+                const int use_f32 = prec && !(flags & HF_FP64_ONLY);
+                a.stage_stride = use_f32 ? fp32_stage_stride(X, ci) : 0;
+                a.kt = nullptr;
+                a.ktB = nullptr;
+                a.kstride = 0;
+                if (X.ket_soa && X.ket_tab[Yc].p) {
+                    const long long st_ = X.ket_stride[Yc];
+                    const double* t64 = X.ket_tab[Yc].as<double>();
+                    const float* t32 = (const float*)(t64 + 9 * (size_t)X.maxpp * st_);
+                    a.kt = use_f32 ? (const void*)t32 : (const void*)t64;
+                    a.ktB = t32 + 9 * (size_t)X.maxpp * st_;
+                    a.kstride = st_;
+                }
+                // a class too small to fill the GPU with one thread per quartet shares each quartet's
+                // primitive work among a lane group instead (shorter latency, same result)
+                const int lanes = (!use_f32 && q1 - q0 < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
+                const long long blocks = ((q1 - q0) * lanes + kEriThreads - 1) / kEriThreads;
+                const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
+                kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st, lanes);
+                HF_CUDA(cudaGetLastError());
+            }
+            if (ev) HF_CUDA(cudaEventRecord(ev[4 * ci + 2 * prec + 1], st));
+        }
+    }
+    return HF_OK;
+}
+
+extern "C" {
+
 int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
                   int flags)
 {
@@ -640,7 +725,8 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
     const size_t NN = (size_t)N * N;
     const bool dev = (flags & HF_PTR_DEVICE) != 0;
     const bool timing = (flags & HF_TIMING) != 0 && stats;
-    // 1. density in, check, raw-normalised copies
+    // 1. density in, check, raw-normalised copies.  The check's flag stays on the device: the ERI,
+    // assembly and energy kernels do nothing when it is set, and the host reads it once, at the end.
     const double* dP = P;
     if (!dev) {
         HF_CUDA(cudaMemcpyAsync(X.staging_P.p, P, NN * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -650,72 +736,41 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
     HF_CUDA(cudaMemsetAsync(X.bad.p, 0, sizeof(int), st));
     KCHK(launch_scale_density(N, dP, S->comp_norm.as<double>(), S->P64.as<double>(),
                               S->P32.p ? S->P32.as<float>() : nullptr, X.bad.as<int>(), st));
-    int bad = 0;
-    HF_CUDA(cudaMemcpyAsync(&bad, X.bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    HF_CUDA(cudaStreamSynchronize(st));
-    if (bad) return fail(HF_E_INVALID, "hf_fock_build: density is not finite or not symmetric");
     // 2. ERI + digestion, one launch per class and precision
     EriArgs a;
     memset(&a, 0, sizeof(a));
     TRY(begin_accumulate(X, a, st));
     if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 1], st));
-    a.pairs = S->pairs.as<PairHdr>();
-    a.prims64 = S->prims64.p;
-    a.prims32 = S->prims32.p;
-    a.N = N;
     a.P64 = S->P64.as<double>();
     a.P32 = S->P32.p ? S->P32.as<float>() : nullptr;
-    a.boys64 = ctx->boys64.as<double>();
-    a.boys32 = ctx->boys32.as<float>();
-    a.prim_tau = S->th.prim_tau;
+    a.bad = X.bad.as<int>();
     if (stats) HF_CUDA(cudaMemsetAsync(X.prim_count.p, 0, sizeof(unsigned long long) * 2 * kNumClasses, st));
-    for (int ci = 0; ci < kNumClasses; ci++) {
-        const auto& pl = S->plan[ci];
-        const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
-        a.bra = S->class_ids[Xc].as<int>();
-        a.ket = S->class_ids[Yc].as<int>();
-        a.n_bra = S->class_count[Xc];
-        a.same = Xc == Yc;
-        for (int prec = 0; prec < 2; prec++) {
-            const long long n = prec ? pl.n32 : pl.n64;
-            if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * ci + 2 * prec], st));
-            a.prim_count = stats ? X.prim_count.as<unsigned long long>() + 2 * ci + prec : nullptr;
-            if (n > 0) {
-                a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
-                a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
-                a.chunk = prec ? pl.chunk32.as<int>() : pl.chunk64.as<int>();
-                a.n_quartets = n;
-                const int use_f32 = prec && !(flags & HF_FP64_ONLY);
-                a.stage_stride = use_f32 ? fp32_stage_stride(X, ci) : 0;
-                // a class too small to fill the GPU with one thread per quartet shares each quartet's
-                // primitive work among a lane group instead (shorter latency, same result)
-                const int lanes = (!use_f32 && n < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
-                const long long blocks = (n * lanes + kEriThreads - 1) / kEriThreads;
-                const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
-                kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st, lanes);
-                HF_CUDA(cudaGetLastError());
-            }
-            if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * ci + 2 * prec + 1], st));
-        }
-    }
+    TRY(launch_eri_classes(S, a, 0, 1, flags, timing ? ctx->ev : nullptr,
+                           stats ? X.prim_count.as<unsigned long long>() : nullptr));
     TRY(end_accumulate(X, st));
     if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 2], st));
-    // 3. symmetrise and assemble
+    // 3. symmetrise and assemble (skipped on the device when the density was rejected)
     double* dF = dev && F ? F : S->F.as<double>();
     double* dJ = dev ? J : (J ? X.staging_out.as<double>() : nullptr);
     double* dK = dev ? K : (K ? X.staging_out.as<double>() + NN : nullptr);
     KCHK(launch_assemble(N, S->Jt.as<double>(), S->Kt.as<double>(), S->comp_norm.as<double>(), S->H.as<double>(), dJ,
-                         dK, dF, st));
+                         dK, dF, X.bad.as<int>(), st));
     if (E_elec) KCHK(launch_energy(N, dP, S->H.as<double>(), dF, S->Ebuf.as<double>(), S->Ebuf.as<double>() + 256, st));
     if (timing) HF_CUDA(cudaEventRecord(ctx->ev[4 * kNumClasses + 3], st));
-    if (!dev) {
+    int bad = 0;
+    double e_host = 0.0;
+    HF_CUDA(cudaMemcpyAsync(&bad, X.bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (E_elec) HF_CUDA(cudaMemcpyAsync(&e_host, S->Ebuf.as<double>() + 256, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));
+    HF_CUDA(cudaGetLastError());
+    if (bad) return fail(HF_E_INVALID, "hf_fock_build: density is not finite or not symmetric");
+    if (!dev) {  // host outputs are written only once the density is known to be valid
         if (F) HF_CUDA(cudaMemcpyAsync(F, dF, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
         if (J) HF_CUDA(cudaMemcpyAsync(J, dJ, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
         if (K) HF_CUDA(cudaMemcpyAsync(K, dK, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HF_CUDA(cudaStreamSynchronize(st));
     }
-    if (E_elec) HF_CUDA(cudaMemcpyAsync(E_elec, S->Ebuf.as<double>() + 256, sizeof(double), cudaMemcpyDeviceToHost, st));
-    HF_CUDA(cudaStreamSynchronize(st));
-    HF_CUDA(cudaGetLastError());
+    if (E_elec) *E_elec = e_host;
     if (stats) {
         unsigned long long pc[2 * kNumClasses];
         HF_CUDA(cudaMemcpy(pc, X.prim_count.p, sizeof(pc), cudaMemcpyDeviceToHost));
@@ -771,22 +826,12 @@ int hf_fock_build_partial(hf_system* S, const double* P, int shard, int n_shards
     HF_CUDA(cudaMemsetAsync(X.bad.p, 0, sizeof(int), st));
     KCHK(launch_scale_density(N, dP, S->comp_norm.as<double>(), S->P64.as<double>(),
                               S->P32.p ? S->P32.as<float>() : nullptr, X.bad.as<int>(), st));
-    int bad = 0;
-    HF_CUDA(cudaMemcpyAsync(&bad, X.bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    HF_CUDA(cudaStreamSynchronize(st));
-    if (bad) return fail(HF_E_INVALID, "hf_fock_build_partial: density is not finite or not symmetric");
     EriArgs a;
     memset(&a, 0, sizeof(a));
     TRY(begin_accumulate(X, a, st));
-    a.pairs = S->pairs.as<PairHdr>();
-    a.prims64 = S->prims64.p;
-    a.prims32 = S->prims32.p;
-    a.N = N;
     a.P64 = S->P64.as<double>();
     a.P32 = S->P32.p ? S->P32.as<float>() : nullptr;
-    a.boys64 = ctx->boys64.as<double>();
-    a.boys32 = ctx->boys32.as<float>();
-    a.prim_tau = S->th.prim_tau;
+    a.bad = X.bad.as<int>();
     if ((flags & HF_DENSITY_SCREEN) && S->th.schwarz_tau > 0.0) {
         if (!X.dsh.p) TRY(X.dsh.alloc(sizeof(float) * (size_t)S->n_shells * S->n_shells));
         KCHK(launch_shell_block_max(S->n_shells, N, S->sh_l.as<int>(), S->sh_bf0.as<int>(), dP, X.dsh.as<float>(),
@@ -795,43 +840,63 @@ int hf_fock_build_partial(hf_system* S, const double* P, int shard, int n_shards
         a.n_sh = S->n_shells;
         a.dtau = (float)S->th.schwarz_tau;
     }
-    for (int ci = 0; ci < kNumClasses; ci++) {
-        const auto& pl = S->plan[ci];
-        const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
-        a.bra = S->class_ids[Xc].as<int>();
-        a.ket = S->class_ids[Yc].as<int>();
-        a.n_bra = S->class_count[Xc];
-        a.same = Xc == Yc;
-        for (int prec = 0; prec < 2; prec++) {
-            const long long n = prec ? pl.n32 : pl.n64;
-            const long long q0 = n * shard / n_shards, q1 = n * (shard + 1) / n_shards;
-            if (q1 <= q0) continue;
-            a.offsets = prec ? pl.offsets32.as<long long>() : pl.offsets64.as<long long>();
-            a.kstart = prec ? pl.kstart32.as<int>() : nullptr;
-            a.chunk = prec ? pl.chunk32.as<int>() : pl.chunk64.as<int>();
-            a.q_begin = q0;
-            a.n_quartets = q1;
-            const int use_f32 = prec && !(flags & HF_FP64_ONLY);
-            a.stage_stride = use_f32 ? fp32_stage_stride(X, ci) : 0;
-            const int lanes = (!use_f32 && q1 - q0 < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
-            const long long blocks = ((q1 - q0) * lanes + kEriThreads - 1) / kEriThreads;
-            const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
-            kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st, lanes);
-            HF_CUDA(cudaGetLastError());
-        }
-    }
+    TRY(launch_eri_classes(S, a, shard, n_shards, flags, nullptr, nullptr));
     TRY(end_accumulate(X, st));
-    // J and K of this shard (no H): assembly with a zero core Hamiltonian is F = J - K/2; use the
-    // F output of the assembly kernel only as scratch
+    // J and K of this shard (no H): the assembly kernel's F output is only scratch here
     double* dJ = dev ? J : X.staging_out.as<double>();
     double* dK = dev ? K : X.staging_out.as<double>() + NN;
     KCHK(launch_assemble(N, S->Jt.as<double>(), S->Kt.as<double>(), S->comp_norm.as<double>(), S->H.as<double>(), dJ,
-                         dK, S->F.as<double>(), st));
+                         dK, S->F.as<double>(), X.bad.as<int>(), st));
+    int bad = 0;
+    HF_CUDA(cudaMemcpyAsync(&bad, X.bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaStreamSynchronize(st));
+    if (bad) return fail(HF_E_INVALID, "hf_fock_build_partial: density is not finite or not symmetric");
     if (!dev) {
         HF_CUDA(cudaMemcpyAsync(J, dJ, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
         HF_CUDA(cudaMemcpyAsync(K, dK, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HF_CUDA(cudaStreamSynchronize(st));
     }
+    return HF_OK;
+}
+
+// F = H + J - K/2 (and E_elec) from J and K summed over the shards of a sharded build.
+int hf_fock_assemble(hf_system* S, const double* P, const double* J, const double* K, double* F, double* E_elec,
+                     int flags)
+{
+    if (!S || !J || !K || !F) return fail(HF_E_INVALID, "hf_fock_assemble: NULL system, J, K or F");
+    if (E_elec && !P) return fail(HF_E_INVALID, "hf_fock_assemble: the energy needs the density P");
+    DeviceGuard g(S->ctx->device);
+    hf_system& X = *S;
+    cudaStream_t st = S->ctx->stream;
+    const int N = S->n_bf;
+    const size_t NN = (size_t)N * N;
+    const bool dev = (flags & HF_PTR_DEVICE) != 0;
+    const double *dJ = J, *dK = K, *dP = P;
+    double* dF = dev ? F : S->F.as<double>();
+    if (!dev) {  // staging: J and K in staging_out, P in staging_P
+        HF_CUDA(cudaMemcpyAsync(X.staging_out.p, J, NN * sizeof(double), cudaMemcpyHostToDevice, st));
+        HF_CUDA(cudaMemcpyAsync(X.staging_out.as<double>() + NN, K, NN * sizeof(double), cudaMemcpyHostToDevice, st));
+        dJ = X.staging_out.as<double>();
+        dK = dJ + NN;
+        if (P) {
+            HF_CUDA(cudaMemcpyAsync(X.staging_P.p, P, NN * sizeof(double), cudaMemcpyHostToDevice, st));
+            dP = X.staging_P.as<double>();
+        }
+    }
+    HF_CUDA(cudaMemsetAsync(X.bad.p, 0, sizeof(int), st));
+    KCHK(launch_fock_from_jk((long long)NN, S->H.as<double>(), dJ, dK, dF, X.bad.as<int>(), st));
+    if (E_elec) KCHK(launch_energy(N, dP, S->H.as<double>(), dF, S->Ebuf.as<double>(), S->Ebuf.as<double>() + 256, st));
+    int bad = 0;
+    double e_host = 0.0;
+    HF_CUDA(cudaMemcpyAsync(&bad, X.bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (E_elec) HF_CUDA(cudaMemcpyAsync(&e_host, S->Ebuf.as<double>() + 256, sizeof(double), cudaMemcpyDeviceToHost, st));
     HF_CUDA(cudaStreamSynchronize(st));
+    if (bad) return fail(HF_E_INVALID, "hf_fock_assemble: J or K is not finite");
+    if (!dev) {
+        HF_CUDA(cudaMemcpyAsync(F, dF, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HF_CUDA(cudaStreamSynchronize(st));
+    }
+    if (E_elec) *E_elec = e_host;
     return HF_OK;
 }
 }  // extern "C"

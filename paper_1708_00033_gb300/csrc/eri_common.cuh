@@ -25,6 +25,43 @@ struct PrimPair {
     float B;             // primitive-pair Schwarz bound sqrt(max |[ab|ab]|), normalised components
 };
 
+// Ket primitive-pair records as the generated quartet functions read them.
+//   KetAos: the pair's own records (PrimPair array at prims + prim0, or a shared-memory copy of them);
+//   KetSoa: the ket's column of its class's ket table, a field-major copy of every significant pair's
+//           records in class-list order (field f of record i of ket k at f9[(9 i + f) stride + k], bound
+//           at fB[i stride + k]): the 32 lanes of a warp, which hold consecutive kets of a class list,
+//           read 32 consecutive words per field instead of 32 scattered records.
+template <typename real>
+struct KetAos {
+    const PrimPair<real>* __restrict__ r;
+    __device__ __forceinline__ PrimPair<real> rec(int i) const { return r[i]; }
+    __device__ __forceinline__ float B(int i) const { return r[i].B; }
+};
+
+template <typename real>
+struct KetSoa {
+    const real* __restrict__ f9;
+    const float* __restrict__ fB;
+    long long stride;
+    __device__ __forceinline__ PrimPair<real> rec(int i) const
+    {
+        const real* q = f9 + (long long)i * 9 * stride;
+        PrimPair<real> x;
+        x.p = __ldg(q);
+        x.Px = __ldg(q + stride);
+        x.Py = __ldg(q + 2 * stride);
+        x.Pz = __ldg(q + 3 * stride);
+        x.PAx = __ldg(q + 4 * stride);
+        x.PAy = __ldg(q + 5 * stride);
+        x.PAz = __ldg(q + 6 * stride);
+        x.K = __ldg(q + 7 * stride);
+        x.oo2p = __ldg(q + 8 * stride);
+        x.B = __ldg(fB + (long long)i * stride);
+        return x;
+    }
+    __device__ __forceinline__ float B(int i) const { return __ldg(fB + (long long)i * stride); }
+};
+
 // Boys tables, rows T_k = k / 32 for k = 0..kBoysRows-1 (T < 60), stored in
 // Taylor-coefficient form so that evaluation is a pure Horner chain:
 //   FP64 row: c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..6) at m*7 + j,
@@ -41,18 +78,31 @@ constexpr double kBoysTmax = 60.0;
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
-// F_m(T), m = 0..L.  Below T = 60: Taylor expansion about the nearest grid
-// point T_k (|T - T_k| <= 1/64; seven terms, truncation < 5e-17 relative),
-// using dF_m/dT = -F_{m+1}; for L >= 2 only F_L is expanded and the rest
-// follow from the downward recursion F_m = (2T F_{m+1} + e^{-T}) / (2m+1),
-// with e^{-T} = e^{-T_k} e^{T_k - T} expanded the same way.  Above: F_0 =
-// sqrt(pi/T)/2 and the upward recursion F_{m+1} = (2m+1) F_m / (2T)
-// (e^{-T} < 1e-26 is dropped).  The grid index is the integer that
-// T*32 + 1.5*2^52 rounds to, read from the low word of the sum.
+// Switch points of the asymptotic form F_m(T) ~ (2m-1)!! / 2^(m+1) sqrt(pi / T^(2m+1)), by the highest
+// order L evaluated: from these T on, its relative error (the dropped terms carry e^{-T}) is below half
+// an ulp for every m <= L, in FP64 (2^-54) and FP32 (2^-25), computed from the incomplete gamma function
+// at 40 digits.  Below them the Taylor tables are used.
+__host__ __device__ constexpr double boys_switch64(int L)
+{
+    return L == 0 ? 36.0 : L == 1 ? 40.0 : L == 2 ? 43.0 : L == 3 ? 46.0 : L == 4 ? 49.0 : L == 5 ? 52.0
+         : L == 6 ? 54.0 : L == 7 ? 57.0 : 59.0;
+}
+__host__ __device__ constexpr float boys_switch32(int L)
+{
+    return L == 0 ? 16.0f : L == 1 ? 19.0f : L == 2 ? 22.0f : L == 3 ? 25.0f : L == 4 ? 27.0f : L == 5 ? 29.0f
+         : L == 6 ? 31.0f : L == 7 ? 33.0f : 35.0f;
+}
+
+// F_m(T), m = 0..L.  Below boys_switch64(L) (<= 59, inside the tables' T < 60): Taylor expansion about the
+// nearest grid point T_k (|T - T_k| <= 1/64; seven terms, truncation < 5e-17 relative), using
+// dF_m/dT = -F_{m+1}; for L >= 2 only F_L is expanded and the rest follow from the downward recursion
+// F_m = (2T F_{m+1} + e^{-T}) / (2m+1), with e^{-T} = e^{-T_k} e^{T_k - T} expanded the same way.  Above:
+// F_0 = sqrt(pi/T)/2 and the upward recursion F_{m+1} = (2m+1) F_m / (2T) (the e^{-T} terms dropped).
+// The grid index is the integer that T*32 + 1.5*2^52 rounds to, read from the low word of the sum.
 template <int L>
 __device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double* F)
 {
-    if (T < kBoysTmax) {
+    if (T < boys_switch64(L)) {
         const double big = 6755399441055744.0;  // 1.5 * 2^52
         const double t = fma(T, 32.0, big);
         const int k = __double2loint(t);
@@ -85,11 +135,11 @@ __device__ __forceinline__ void boys_eval(double T, const double* __restrict__ t
 }
 
 // Single-precision variant for the mixed path: four Taylor terms (truncation
-// < 3e-9 relative), same recursions.
+// < 3e-9 relative), same recursions, asymptotic from boys_switch32(L).
 template <int L>
 __device__ __forceinline__ void boys_eval(float T, const float* __restrict__ tab, float* F)
 {
-    if (T < (float)kBoysTmax) {
+    if (T < boys_switch32(L)) {
         const float big = 12582912.0f;  // 1.5 * 2^23
         const float t = fmaf(T, 32.0f, big);
         const int k = __float_as_int(t) - 0x4B400000;
@@ -188,9 +238,10 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
 // Kernels and host launchers of one class.  The digestion weight of a unique
 // shell quartet is f = 1/((1+d_AB)(1+d_CD)(1+d_AB,CD)).
 #define ERI_CLASS_KERNELS(NAME, X, Y, GL)                                                                    \
-    template <typename real, int GK>                                                                         \
+    template <typename real, int GK, bool SOA>                                                               \
     __global__ void __launch_bounds__(kEriThreads) k_eri_##NAME(const EriArgs a)                            \
     {                                                                                                        \
+        if (a.bad && *a.bad) return; /* rejected density: grid-uniform exit, outputs untouched */            \
         const PrimPair<real>* prims = (const PrimPair<real>*)(sizeof(real) == 8 ? a.prims64 : a.prims32);   \
         const real* P = (const real*)(sizeof(real) == 8 ? (const void*)a.P64 : (const void*)a.P32);          \
         const real* bt = (const real*)(sizeof(real) == 8 ? (const void*)a.boys64 : (const void*)a.boys32);  \
@@ -209,11 +260,12 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
             const bool valid = q < a.n_quartets;                                                             \
             PairHdr hb, hk;                                                                                  \
             double f = 1.0;                                                                                  \
+            int k = 0;                                                                                       \
             if (valid) {                                                                                     \
                 const long long c = q >> kChunkShift;                                                        \
                 const int b = a.chunk ? find_bra_in(a.offsets, a.chunk[c], a.chunk[c + 1], q)                 \
                                       : find_bra(a.offsets, a.n_bra, q);                                     \
-                const int k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                        \
+                k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                                  \
                 hb = a.pairs[a.bra[b]];                                                                      \
                 hk = a.pairs[a.ket[k]];                                                                      \
                 if (hb.A == hb.B) f *= 0.5;                                                                  \
@@ -230,7 +282,7 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
                 pt = ptau / fmaxf(dm, 1e-30f);                                                               \
             }                                                                                                \
             const PrimPair<real>* kst = nullptr;                                                            \
-            if constexpr (sizeof(real) == 4) {                                                               \
+            if constexpr (sizeof(real) == 4 && !SOA) {                                                       \
                 if (a.stage_stride > 0) { /* warp-uniform: copy the 32 lanes' ket records */                 \
                     float* wsm = kstage_smem + (size_t)(threadIdx.x >> 5) * 32 * a.stage_stride;             \
                     const int wl = threadIdx.x & 31;                                                         \
@@ -246,8 +298,15 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
                     kst = (const PrimPair<real>*)(wsm + wl * a.stage_stride);                                \
                 }                                                                                            \
             }                                                                                                \
-            nprimq += quartet_##NAME<real, GK>(hb, hk, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane, live,  \
-                                               kst);                                                         \
+            if constexpr (SOA) {                                                                             \
+                const KetSoa<real> kv{(const real*)a.kt + k, a.ktB + k, a.kstride};                          \
+                nprimq += quartet_##NAME<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
+                                                   live);                                                    \
+            } else {                                                                                         \
+                const KetAos<real> kv{kst ? kst : prims + hk.prim0};                                         \
+                nprimq += quartet_##NAME<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
+                                                   live);                                                    \
+            }                                                                                                \
         }                                                                                                    \
         if (a.prim_count) {                                                                                  \
             const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \
@@ -256,22 +315,33 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
     }                                                                                                        \
     void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s, int lanes)   \
     {                                                                                                        \
-        if (use_f32)                                                                                         \
-            k_eri_##NAME<float, 1><<<grid, block, stage_bytes(a.stage_stride, block), s>>>(a);              \
-        else if (lanes > 1)                                                                                  \
-            k_eri_##NAME<double, (GL)><<<grid, block, 0, s>>>(a);                                            \
-        else                                                                                                 \
-            k_eri_##NAME<double, 1><<<grid, block, 0, s>>>(a);                                               \
+        const bool soa = a.kt != nullptr;                                                                    \
+        if (use_f32) {                                                                                       \
+            if (soa)                                                                                         \
+                k_eri_##NAME<float, 1, true><<<grid, block, 0, s>>>(a);                                      \
+            else                                                                                             \
+                k_eri_##NAME<float, 1, false><<<grid, block, stage_bytes(a.stage_stride, block), s>>>(a);   \
+        } else if (lanes > 1) {                                                                              \
+            if (soa)                                                                                         \
+                k_eri_##NAME<double, (GL), true><<<grid, block, 0, s>>>(a);                                  \
+            else                                                                                             \
+                k_eri_##NAME<double, (GL), false><<<grid, block, 0, s>>>(a);                                 \
+        } else {                                                                                             \
+            if (soa)                                                                                         \
+                k_eri_##NAME<double, 1, true><<<grid, block, 0, s>>>(a);                                     \
+            else                                                                                             \
+                k_eri_##NAME<double, 1, false><<<grid, block, 0, s>>>(a);                                    \
+        }                                                                                                    \
     }                                                                                                        \
     size_t local_bytes_##NAME()                                                                              \
     {                                                                                                        \
         cudaFuncAttributes fa;                                                                               \
         size_t m = 0;                                                                                        \
-        if (cudaFuncGetAttributes(&fa, k_eri_##NAME<double, 1>) == cudaSuccess) m = fa.localSizeBytes;       \
-        if (cudaFuncGetAttributes(&fa, k_eri_##NAME<double, (GL)>) == cudaSuccess && fa.localSizeBytes > m)  \
-            m = fa.localSizeBytes;                                                                           \
-        if (cudaFuncGetAttributes(&fa, k_eri_##NAME<float, 1>) == cudaSuccess && fa.localSizeBytes > m)      \
-            m = fa.localSizeBytes;                                                                           \
+        const void* fns[] = {(const void*)k_eri_##NAME<double, 1, false>, (const void*)k_eri_##NAME<double, (GL), false>, \
+                             (const void*)k_eri_##NAME<float, 1, false>, (const void*)k_eri_##NAME<double, 1, true>,   \
+                             (const void*)k_eri_##NAME<double, (GL), true>, (const void*)k_eri_##NAME<float, 1, true>}; \
+        for (const void* fn : fns)                                                                           \
+            if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.localSizeBytes > m) m = fa.localSizeBytes; \
         if (cudaFuncGetAttributes(&fa, k_eri_batch_##NAME) == cudaSuccess && fa.localSizeBytes > m)          \
             m = fa.localSizeBytes;                                                                           \
         cudaGetLastError();                                                                                  \
@@ -297,7 +367,8 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
             h.nprim = 1;                                                                                     \
         }                                                                                                    \
         double qm = 0.0;                                                                                     \
-        quartet_##NAME<double, 1>(h, h, pr, a.boys64, nullptr, 0, 1.0, nullptr, nullptr, &qm, 0.0f, 0, true); \
+        quartet_##NAME<double, 1>(h, h, KetAos<double>{pr + h.prim0}, pr, a.boys64, nullptr, 0, 1.0, nullptr,  \
+                                  nullptr, &qm, 0.0f, 0, true);                                              \
         if (item == 0)                                                                                       \
             a.Q[pid] = sqrt(qm);                                                                             \
         else                                                                                                 \
@@ -347,7 +418,8 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
                 } else {                                                                                     \
                     hb = hk = mc.pairs[mc.bra[0]];                                                           \
                 }                                                                                            \
-                quartet_##NAME<double, (GL)>(hb, hk, (const PrimPair<double>*)mc.prims64, a.boys64, mc.P64, mc.N, f, \
+                const PrimPair<double>* mp = (const PrimPair<double>*)mc.prims64;                            \
+                quartet_##NAME<double, (GL)>(hb, hk, KetAos<double>{mp + hk.prim0}, mp, a.boys64, mc.P64, mc.N, f, \
                                              mc.Jt, mc.Kt, nullptr, ptau, lane, valid);                      \
             }                                                                                                \
         }                                                                                                    \

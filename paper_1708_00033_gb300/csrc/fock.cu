@@ -29,10 +29,10 @@ __global__ void k_scale_density(int N, const double* __restrict__ P, const doubl
 
 __global__ void k_assemble(int N, const double* __restrict__ Jt, const double* __restrict__ Kt,
                            const double* __restrict__ n, const double* __restrict__ H, double* __restrict__ J,
-                           double* __restrict__ K, double* __restrict__ F)
+                           double* __restrict__ K, double* __restrict__ F, const int* __restrict__ bad)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)N * N) return;
+    if (t >= (long long)N * N || (bad && *bad)) return;
     const int i = (int)(t / N), j = (int)(t % N);
     const size_t tt = (size_t)j * N + i;
     const double s = 0.5 * n[i] * n[j];
@@ -136,10 +136,29 @@ int launch_scale_density(int N, const double* P, const double* comp_norm, double
 }
 
 int launch_assemble(int N, const double* Jt, const double* Kt, const double* comp_norm, const double* H, double* J,
-                    double* K, double* F, cudaStream_t s)
+                    double* K, double* F, const int* bad, cudaStream_t s)
 {
     const long long n = (long long)N * N;
-    if (n > 0) k_assemble<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(N, Jt, Kt, comp_norm, H, J, K, F);
+    if (n > 0) k_assemble<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(N, Jt, Kt, comp_norm, H, J, K, F, bad);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// F = H + J - K/2 from already symmetrised J and K (the assembly of a sharded build after the sum over
+// shards); *bad is set when J or K holds a non-finite value.
+__global__ void k_fock_from_jk(long long n, const double* __restrict__ H, const double* __restrict__ J,
+                               const double* __restrict__ K, double* __restrict__ F, int* __restrict__ bad)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double j = J[t], k = K[t];
+    if (!isfinite(j) || !isfinite(k)) atomicOr(bad, 1);
+    F[t] = H[t] + j - 0.5 * k;
+}
+
+int launch_fock_from_jk(long long n, const double* H, const double* J, const double* K, double* F, int* bad,
+                        cudaStream_t s)
+{
+    if (n > 0) k_fock_from_jk<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, H, J, K, F, bad);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -383,28 +383,27 @@ def gen_class(X, Y):
     out.append(f"// primitive staircase round-robin and sum their accumulators with butterfly shuffles; lane 0")
     out.append(f"// then runs the horizontal recurrence and the digestion.  Called warp-uniformly; a lane with")
     out.append(f"// valid == false takes part in the shuffles only.")
-    out.append(f"template <typename real, int G>")
-    out.append(f"__device__ __forceinline__ int quartet_{name}(const PairHdr& hb, const PairHdr& hk,"
+    out.append(f"template <typename real, int G, typename KV>")
+    out.append(f"__device__ __forceinline__ int quartet_{name}(const PairHdr& hb, const PairHdr& hk, const KV& kv,"
                f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
     out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
-    out.append(f"    float ptau, int lane, bool valid, const PrimPair<real>* kstage = nullptr)")
+    out.append(f"    float ptau, int lane, bool valid)")
     out.append("{")
     out.append("    // surviving primitive quartets form a staircase (pairs sorted by bound): bra primitive ib")
     out.append("    // pairs with the first nk(ib) ket primitives, nk non-increasing; one flat loop over it.")
-    out.append("    // kstage: the ket's records staged in shared memory by the caller (nullptr: read them globally)")
+    out.append("    // kv: the ket's records (KetAos: the pair's record array; KetSoa: its column of the class's ket table)")
     out.append("    const PrimPair<real>* __restrict__ bpp = prims + hb.prim0;")
-    out.append("    const PrimPair<real>* __restrict__ kpp = kstage ? kstage : prims + hk.prim0;")
     out.append("    const int nbp = hb.nprim;")
     out.append("    int nkb = hk.nprim;")
     out.append("    int total = 0;")
     out.append("    if (valid) {")
     out.append("        for (int ib = 0, c = nkb; ib < nbp; ib++) {")
     out.append("            const float Bb = bpp[ib].B;")
-    out.append("            while (c > 0 && Bb * kpp[c - 1].B < ptau) c--;")
+    out.append("            while (c > 0 && Bb * kv.B(c - 1) < ptau) c--;")
     out.append("            if (c == 0) break;")
     out.append("            total += c;")
     out.append("        }")
-    out.append("        while (nkb > 0 && bpp[0].B * kpp[nkb - 1].B < ptau) nkb--;")
+    out.append("        while (nkb > 0 && bpp[0].B * kv.B(nkb - 1) < ptau) nkb--;")
     out.append("    }")
     out.append("    int nq = 0;")
     for l in acc_decl:
@@ -416,7 +415,7 @@ def gen_class(X, Y):
     out.append("            ik = 0;")
     out.append("            ib++;")
     out.append("            if (ib < nbp)")
-    out.append("                while (nkb > 0 && bpp[ib].B * kpp[nkb - 1].B < ptau) nkb--;")
+    out.append("                while (nkb > 0 && bpp[ib].B * kv.B(nkb - 1) < ptau) nkb--;")
     out.append("        }")
     out.append("    };")
     out.append("    if (G > 1)")
@@ -427,7 +426,7 @@ def gen_class(X, Y):
     out.append("        for (int s = 0; s < G; s++) advance();")
     out.append("        nq++;")
     out.append("        const PrimPair<real> bp = bpp[cib];")
-    out.append("        const PrimPair<real> kp = kpp[cik];")
+    out.append("        const PrimPair<real> kp = kv.rec(cik);")
     out.append("        const real bK = bp.K, bo2p = bp.oo2p;")
     for a in AX:
         if f"PA{a}" in used:

@@ -273,6 +273,45 @@ __global__ void k_guess_scatter(long long np, int N, const float* __restrict__ Y
         }
 }
 
+// Training targets of every atom pair: T[t][head block] = the pair's block of P, mask 1 there, 0 elsewhere.
+__global__ void k_guess_targets(long long np, int N, const double* __restrict__ P, const PairMeta* __restrict__ meta,
+                                float* __restrict__ T, float* __restrict__ mask)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np * kOut) return;
+    const long long t = e / kOut;
+    const int o = (int)(e - t * kOut);
+    const PairMeta pm = meta[t];
+    const int h = pm.head, o0 = head_off(h), nc = head_cols(h);
+    const int r = (o - o0) / nc, c = (o - o0) % nc;
+    const bool in = o >= o0 && o < o0 + head_rows(h) * nc;
+    T[e] = in ? (float)P[(size_t)(pm.row0 + r) * N + pm.col0 + c] : 0.0f;
+    mask[e] = in ? 1.0f : 0.0f;
+}
+
+// SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014) applied to seed + (i + 1) * golden gamma.
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long i)
+{
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Minibatch of step k: sample j is row splitmix64(seed, k * batch + j) mod n of the dataset.
+__global__ void k_draw_batch(long long n, int batch, unsigned long long seed, long long step,
+                             const float* __restrict__ X, const float* __restrict__ T, const float* __restrict__ M,
+                             float* __restrict__ Xb, float* __restrict__ Tb, float* __restrict__ Mb)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)batch * kOut) return;
+    const int j = (int)(e / kOut), o = (int)(e % kOut);
+    const long long row = (long long)(splitmix64(seed, (unsigned long long)(step * batch + j)) % (unsigned long long)n);
+    Tb[e] = T[row * kOut + o];
+    Mb[e] = M[row * kOut + o];
+    if (o < kFeat) Xb[(size_t)j * kFeat + o] = X[row * kFeat + o];
+}
+
 __global__ void k_trace_ps(int N, const double* __restrict__ P, const double* __restrict__ S, double* __restrict__ part)
 {
     __shared__ double sm[256];
@@ -342,7 +381,8 @@ struct hf_model {
     int step = 0;
     // activation workspace
     DevBuf Z1, H1, Z2, H2, Y, dY, dH, dZ, part, lossbuf;
-    long long cap = 0;
+    DevBuf Xb, Tb, Mb;  // minibatch drawn by hf_guess_train
+    long long cap = 0, bcap = 0;
     int reserve(long long n)
     {
         if (n <= cap) return HF_OK;
@@ -377,13 +417,14 @@ static int forward(hf_model* M, int n, const float* X, cudaStream_t st)
 
 // gradients of loss = sum(mask (Y - T)^2) / count into M->g
 static int backward(hf_model* M, int n, const float* X, const float* T, const float* mask, float* loss,
-                    cudaStream_t st)
+                    cudaStream_t st, float* loss_dev = nullptr)
 {
     // loss = (1/n) sum_samples sum_outputs mask (Y - T)^2, masks being 0/1 per output
     const long long ny = (long long)n * kOut;
     const float inv = 1.0f / (float)n;
     k_mse<<<128, 256, 0, st>>>(ny, M->Y.as<float>(), T, mask, inv, M->dY.as<float>(), M->part.as<double>());
-    if (loss) k_sum_parts<<<1, 256, 0, st>>>(128, M->part.as<double>(), inv, M->lossbuf.as<float>());
+    if (loss || loss_dev)
+        k_sum_parts<<<1, 256, 0, st>>>(128, M->part.as<double>(), inv, loss_dev ? loss_dev : M->lossbuf.as<float>());
     // layer 3
     sgemm<float>(kOut, kWidth, n, M->dY.as<float>(), kOut, true, M->H2.as<float>(), kWidth, false, nullptr, nullptr,
                  M->G(4), kWidth, false, false, st);
@@ -404,10 +445,21 @@ static int backward(hf_model* M, int n, const float* X, const float* T, const fl
     sgemm<float>(kWidth, kFeat, n, M->dZ.as<float>(), kWidth, true, X, kFeat, false, nullptr, nullptr, M->G(0), kFeat,
                  false, false, st);
     k_colsum<<<(kWidth + 127) / 128, 128, 0, st>>>(n, kWidth, M->dZ.as<float>(), M->G(1));
-    if (loss) {
+    if (loss && !loss_dev) {
         HF_CUDA(cudaMemcpyAsync(loss, M->lossbuf.p, sizeof(float), cudaMemcpyDeviceToHost, st));
     }
     return cudaGetLastError() == cudaSuccess ? HF_OK : cuda_status(cudaGetLastError(), "guess backward");
+}
+
+// One Adam step (beta 0.9 / 0.999, eps 1e-8) on the gradients in M->g with learning rate lr.
+static void adam_step(hf_model* M, float lr, cudaStream_t st)
+{
+    M->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f / (1.0f - powf(b1, (float)M->step)), c2 = 1.0f / (1.0f - powf(b2, (float)M->step));
+    k_adam<<<(unsigned)((M->n_params + 255) / 256), 256, 0, st>>>(M->n_params, M->w.as<float>(), M->g.as<float>(),
+                                                                  M->m.as<float>(), M->v.as<float>(),
+                                                                  M->wb.as<__nv_bfloat16>(), lr, b1, b2, 1e-8f, c1, c2);
 }
 
 extern "C" {
@@ -497,15 +549,52 @@ int hf_model_train_step(hf_model* M, int n, const float* X, const float* T, cons
     if (!(flags & HF_PTR_DEVICE)) return gfail(HF_E_INVALID, "hf_model_train_step: device pointers required");
     if ((rc = forward(M, n, X, st)) != HF_OK) return rc;
     if ((rc = backward(M, n, X, T, mask, loss, st)) != HF_OK) return rc;
-    if (lr > 0.0f) {
-        M->step++;
-        const float b1 = 0.9f, b2 = 0.999f;
-        const float c1 = 1.0f / (1.0f - powf(b1, (float)M->step)), c2 = 1.0f / (1.0f - powf(b2, (float)M->step));
-        k_adam<<<(unsigned)((M->n_params + 255) / 256), 256, 0, st>>>(M->n_params, M->w.as<float>(), M->g.as<float>(),
-                                                                      M->m.as<float>(), M->v.as<float>(),
-                                                                      M->wb.as<__nv_bfloat16>(), lr, b1, b2, 1e-8f, c1,
-                                                                      c2);
+    if (lr > 0.0f) adam_step(M, lr, st);
+    HF_CUDA(cudaStreamSynchronize(st));
+    HF_CUDA(cudaGetLastError());
+    return HF_OK;
+}
+
+int hf_guess_train(hf_model* M, int64_t n, const float* X, const float* T, const float* mask,
+                   const hf_train_opts* opts, float* losses, int flags)
+{
+    if (!M || !X || !T || !mask || !opts || n <= 0) return gfail(HF_E_INVALID, "hf_guess_train: bad arguments");
+    if (!(flags & HF_PTR_DEVICE)) return gfail(HF_E_INVALID, "hf_guess_train: the dataset must be in device memory");
+    if (opts->steps <= 0 || opts->batch < 0 || !(opts->lr >= 0.0f) || !isfinite(opts->lr))
+        return gfail(HF_E_INVALID, "hf_guess_train: bad options");
+    GuessDevice gd(M->ctx->device);
+    cudaStream_t st = M->ctx->stream;
+    const int batch = (int)std::min<int64_t>(opts->batch > 0 ? opts->batch : 2048, n);
+    const float lr = opts->lr > 0.0f ? opts->lr : 1e-3f;
+    int rc = M->reserve(batch);
+    if (rc != HF_OK) return rc;
+    if (batch > M->bcap) {
+        if ((rc = M->Xb.alloc(sizeof(float) * (size_t)batch * kFeat)) ||
+            (rc = M->Tb.alloc(sizeof(float) * (size_t)batch * kOut)) ||
+            (rc = M->Mb.alloc(sizeof(float) * (size_t)batch * kOut))) {
+            M->bcap = 0;
+            return rc;
+        }
+        M->bcap = batch;
     }
+    DevBuf ldev;
+    if ((rc = ldev.alloc(sizeof(float) * (size_t)opts->steps))) return rc;
+    const long long ne = (long long)batch * kOut;
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < opts->steps; k++) {
+        k_draw_batch<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(n, batch, (unsigned long long)opts->seed, k, X, T,
+                                                                  mask, M->Xb.as<float>(), M->Tb.as<float>(),
+                                                                  M->Mb.as<float>());
+        if ((rc = forward(M, batch, M->Xb.as<float>(), st)) != HF_OK) return rc;
+        if ((rc = backward(M, batch, M->Xb.as<float>(), M->Tb.as<float>(), M->Mb.as<float>(), nullptr, st,
+                           ldev.as<float>() + k)) != HF_OK)
+            return rc;
+        // cosine decay from lr to 0 over the run
+        const float lr_k = (float)(lr * 0.5 * (1.0 + cos(pi * (double)k / (double)opts->steps)));
+        if (lr_k > 0.0f) adam_step(M, lr_k, st);
+    }
+    HF_CUDA(cudaGetLastError());
+    if (losses) HF_CUDA(cudaMemcpyAsync(losses, ldev.p, sizeof(float) * (size_t)opts->steps, cudaMemcpyDeviceToHost, st));
     HF_CUDA(cudaStreamSynchronize(st));
     HF_CUDA(cudaGetLastError());
     return HF_OK;
@@ -560,6 +649,41 @@ int hf_guess_features(hf_system* S, float* X, int32_t* meta, int64_t* n_pairs, i
     }
     HF_CUDA(cudaStreamSynchronize(st));
     if (hb) return gfail(HF_E_UNSUPPORTED, "hf_guess_features: only H and O atoms are supported");
+    return HF_OK;
+}
+
+int hf_guess_targets(hf_system* S, const double* P, float* T, float* mask, int flags)
+{
+    if (!S || !P || !T || !mask) return gfail(HF_E_INVALID, "hf_guess_targets: NULL argument");
+    GuessDevice gd(S->device);
+    cudaStream_t st = S->stream;
+    int64_t np = 0;
+    hf_guess_features(S, nullptr, nullptr, &np, 0);
+    const int N = S->n_bf;
+    const bool dev = (flags & HF_PTR_DEVICE) != 0;
+    DevBuf X, meta, Pd, Td, Md;
+    int rc;
+    if ((rc = X.alloc(sizeof(float) * np * kFeat)) || (rc = meta.alloc(sizeof(PairMeta) * np))) return rc;
+    if ((rc = hf_guess_features(S, X.as<float>(), (int32_t*)meta.p, &np, HF_PTR_DEVICE)) != HF_OK) return rc;
+    const double* pp = P;
+    float *tp = T, *mp = mask;
+    if (!dev) {
+        if ((rc = Pd.alloc(sizeof(double) * (size_t)N * N)) || (rc = Td.alloc(sizeof(float) * np * kOut)) ||
+            (rc = Md.alloc(sizeof(float) * np * kOut)))
+            return rc;
+        HF_CUDA(cudaMemcpyAsync(Pd.p, P, sizeof(double) * (size_t)N * N, cudaMemcpyHostToDevice, st));
+        pp = Pd.as<double>();
+        tp = Td.as<float>();
+        mp = Md.as<float>();
+    }
+    const long long ne = np * kOut;
+    k_guess_targets<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(np, N, pp, meta.as<PairMeta>(), tp, mp);
+    HF_CUDA(cudaGetLastError());
+    if (!dev) {
+        HF_CUDA(cudaMemcpyAsync(T, tp, sizeof(float) * ne, cudaMemcpyDeviceToHost, st));
+        HF_CUDA(cudaMemcpyAsync(mask, mp, sizeof(float) * ne, cudaMemcpyDeviceToHost, st));
+    }
+    HF_CUDA(cudaStreamSynchronize(st));
     return HF_OK;
 }
 

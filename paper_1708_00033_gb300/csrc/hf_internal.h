@@ -56,6 +56,11 @@ struct EriArgs {
                                       // (0: ket records read from global memory)
     int n_copies;                     // > 1: block b accumulates into copy b % n_copies of Jt / Kt
     long long copy_stride;            // doubles between copies
+    const int* bad;                   // density-check flag: the kernel does nothing when *bad != 0
+    const void* kt;                   // ket table of the launch's ket class and precision (field-major records
+                                      // in class-list order, see KetSoa); nullptr: records read per pair
+    const float* ktB;                 // primitive-pair bounds of the ket table
+    long long kstride;                // kets per field row of the ket table
 };
 
 struct SchwarzArgs {
@@ -109,6 +114,18 @@ struct EriClassEntry {
 };
 extern const EriClassEntry kEriClasses[kNumClasses];
 
+// Launches the ERI class kernels of one build: for every class and precision, the quartets
+// [n shard / n_shards, n (shard + 1) / n_shards) of its n screened quartets (shard 0 of 1 is the
+// whole build).  `a` carries the fields common to every launch (density, accumulators, tables,
+// screening and flag pointers); the per-class fields are filled here.  flags: HF_FP64_ONLY.
+// ev (nullable): events 4 c + 2 prec and 4 c + 2 prec + 1 are recorded around each class launch;
+// prim_count (nullable): 2 c + prec counts the evaluated primitive quartets of each launch.
+int launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int flags, cudaEvent_t* ev,
+                       unsigned long long* prim_count);
+
+// Device address of the allocation-free build's fixed scratch on the current device (noalloc.cu).
+int noalloc_scratch_address(void** out);
+
 // ---------------------------------------------------------------- errors --
 struct Status {
     int code = HF_OK;
@@ -158,6 +175,7 @@ struct hf_ctx {
     bool events_ready = false;
     int n_systems = 0;            // live systems created on this context
     bool destroy_pending = false;  // hf_destroy was called while systems were alive
+    void* noalloc_scratch = nullptr;  // device address of hf_fock_build_noalloc's fixed scratch
 };
 
 struct hf_system {
@@ -191,6 +209,11 @@ struct hf_system {
     hf::DevBuf Qall, counts, staging_P, staging_out, bad, Bprim, prim_count;
     hf::DevBuf arena_in, arena_mat, arena_sched;  // owners of the views above
     hf::DevBuf dsh;                                // density block maxima for density-weighted screening
+    // ket tables: per pair class, the significant pairs' primitive-pair records in class-list order and
+    // field-major (9 maxpp rows of FP64 fields, 9 maxpp rows of FP32 fields, maxpp rows of bounds)
+    hf::DevBuf ket_tab[hf::kNumPairClasses];
+    long long ket_stride[hf::kNumPairClasses] = {};
+    bool ket_soa = true;  // ERI launches read ket records from the ket tables
     int fock_copies = 1;                           // accumulator copies of Jt / Kt (1: one shared copy)
     hf::DevBuf copies;                             // [2][fock_copies][N*N] when fock_copies > 1
     int maxpp = 0;

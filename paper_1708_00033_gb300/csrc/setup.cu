@@ -291,6 +291,45 @@ __global__ void k_sort_prims(long long n_pairs, const PairHdr* __restrict__ pair
     }
 }
 
+// Ket table of one pair class: record i of the class's k-th pair (ids[k]) at field-major position
+// (9 i + f) stride + k of the FP64 and FP32 field rows, its bound at i stride + k; records past the pair's
+// primitive count are zero (bound 0, so every primitive screen skips them).
+__global__ void k_ket_table(int n, int maxpp, long long stride, const int* __restrict__ ids,
+                            const PairHdr* __restrict__ pairs, const PrimPair<double>* __restrict__ p64,
+                            const PrimPair<float>* __restrict__ p32, double* __restrict__ t64, float* __restrict__ t32,
+                            float* __restrict__ tB)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * maxpp) return;
+    const int i = (int)(t / n), k = (int)(t % n);  // consecutive threads: consecutive kets (coalesced writes)
+    const PairHdr h = pairs[ids[k]];
+    PrimPair<double> r{};
+    PrimPair<float> f{};
+    if (i < h.nprim) {
+        r = p64[h.prim0 + i];
+        f = p32[h.prim0 + i];
+    }
+    const double v64[9] = {r.p, r.Px, r.Py, r.Pz, r.PAx, r.PAy, r.PAz, r.K, r.oo2p};
+    const float v32[9] = {f.p, f.Px, f.Py, f.Pz, f.PAx, f.PAy, f.PAz, f.K, f.oo2p};
+#pragma unroll
+    for (int x = 0; x < 9; x++) {
+        t64[((long long)i * 9 + x) * stride + k] = v64[x];
+        t32[((long long)i * 9 + x) * stride + k] = v32[x];
+    }
+    tB[(long long)i * stride + k] = i < h.nprim ? r.B : 0.0f;
+}
+
+int launch_ket_table(int n, int maxpp, long long stride, const int* ids, const PairHdr* pairs, const void* p64,
+                     const void* p32, double* t64, float* t32, float* tB, cudaStream_t s)
+{
+    const long long items = (long long)n * maxpp;
+    if (items > 0)
+        k_ket_table<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(n, maxpp, stride, ids, pairs,
+                                                                    (const PrimPair<double>*)p64,
+                                                                    (const PrimPair<float>*)p32, t64, t32, tB);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_sort_prims(long long n_pairs, const PairHdr* pairs, const double* Bprim, void* p64, void* p32, cudaStream_t s)
 {
     if (n_pairs > 0)

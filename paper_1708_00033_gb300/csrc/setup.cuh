@@ -19,6 +19,8 @@ int launch_copy_q(long long n, const double* Q, PairHdr* pairs, unsigned long lo
 int launch_class_scatter_sig(long long n, const int* pclass, const double* Q, int X, double qmax, double tau,
                              unsigned* cursor, double* key, int* val, cudaStream_t s);
 int bitonic_sort_desc(double* key, int* val, int n, int n_pad, cudaStream_t s);
+int launch_ket_table(int n, int maxpp, long long stride, const int* ids, const PairHdr* pairs, const void* p64,
+                     const void* p32, double* t64, float* t32, float* tB, cudaStream_t s);
 int launch_sort_prims(long long n_pairs, const PairHdr* pairs, const double* Bprim, void* p64, void* p32, cudaStream_t s);
 int launch_scan(int n, const long long* in, long long* out, cudaStream_t s);
 int launch_sig_scatter(long long n_pairs, long long n_seg, const int* pclass, const double* Q,
@@ -44,7 +46,9 @@ int launch_shell_block_max(int n_sh, int N, const int* l, const int* bf0, const 
 int launch_scale_density(int N, const double* P, const double* comp_norm, double* P64, float* P32, int* bad,
                          cudaStream_t s);
 int launch_assemble(int N, const double* Jt, const double* Kt, const double* comp_norm, const double* H, double* J,
-                    double* K, double* F, cudaStream_t s);
+                    double* K, double* F, const int* bad, cudaStream_t s);
+int launch_fock_from_jk(long long n, const double* H, const double* J, const double* K, double* F, int* bad,
+                        cudaStream_t s);
 int launch_energy(int N, const double* P, const double* H, const double* F, double* partial, double* out,
                   cudaStream_t s);
 

@@ -1,92 +1,117 @@
 """Learned initial guess around the library's MLP kernels.
 
 * make_dataset: seeded water clusters, converged densities from the plain
-  FP64 SCF (hf_scf_run), per-atom-pair features from hf_guess_features and
-  the matching density blocks as targets;
-* train: minibatch Adam steps, each one hf_model_train_step;
+  FP64 SCF (hf_scf_run), per-atom-pair features (hf_guess_features) and the
+  matching density blocks as targets (hf_guess_targets);
+* train: hf_guess_train (minibatch draws, cosine learning-rate decay and Adam
+  steps run in the library);
 * predict: hf_guess_predict (device), with the core-Hamiltonian guess as the
   fallback when the prediction is unusable;
-* evaluate: SCF iterations and time from the learned guess vs the core guess,
+* evaluate: SCF iterations and time from the learned vs the core guess,
   and the difference of the converged energies.
-Weight initialisation is drawn here (seeded numpy) and passed to the library.
+The seeded initial weights are drawn by inputs.guess_init_weights.
 """
 from __future__ import annotations
 
+import json
+import os
+import threading
 import time
 
 import numpy as np
 
 from . import hf, inputs
 
-HEAD_OFF = (0, 225, 300)
-HEAD_SHAPE = ((15, 15), (15, 5), (5, 5))
+init_weights = inputs.guess_init_weights
+
+# Trained weights shipped with the package (written by train_guess.py from plain-SCF densities).
+WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "guess_weights.npz")
 
 
-def init_weights(seed: int = 0) -> np.ndarray:
-    """He-uniform weights, zero biases (float32 vector in the library's layout)."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for fan_in, fan_out in ((16, 256), (256, 256), (256, 325)):
-        lim = np.sqrt(6.0 / fan_in) * (1.0 if fan_out != 325 else 0.1)
-        parts.append(rng.uniform(-lim, lim, size=(fan_out, fan_in)).astype(np.float32).ravel())
-        parts.append(np.zeros(fan_out, dtype=np.float32))
-    return np.concatenate(parts)
+def load_weights(path: str = WEIGHTS_PATH):
+    """(float32 weight vector, metadata dict) of a weight file written by train_guess.py."""
+    with np.load(path) as z:
+        return z["weights"].astype(np.float32), json.loads(str(z["meta"]))
 
 
-def pair_targets(P: np.ndarray, meta: np.ndarray):
-    """Target blocks and 0/1 masks for each pair's head."""
-    n = meta.shape[0]
-    T = np.zeros((n, 325), dtype=np.float32)
-    M = np.zeros((n, 325), dtype=np.float32)
-    for t in range(n):
-        r0, c0, h, _ = (int(x) for x in meta[t])
-        nr, nc = HEAD_SHAPE[h]
-        T[t, HEAD_OFF[h]:HEAD_OFF[h] + nr * nc] = P[r0:r0 + nr, c0:c0 + nc].ravel()
-        M[t, HEAD_OFF[h]:HEAD_OFF[h] + nr * nc] = 1.0
-    return T, M
+def save_weights(path: str, weights: np.ndarray, meta: dict):
+    np.savez_compressed(path, weights=np.asarray(weights, dtype=np.float32), meta=json.dumps(meta))
+
+
+def _cluster_sample(ctx, config, m, lo, hi, tau, prim_tau):
+    geom = inputs.batch_cluster(config, m, lo, hi)
+    basis = inputs.synthetic_basis(geom)
+    s = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=prim_tau)
+    try:
+        r = hf.scf(s, e_tol=1e-9, d_tol=1e-6)
+        X, _ = hf.guess_features(s)
+        T, M = hf.guess_targets(s, r["P"])
+    finally:
+        s.close()
+    return X, T, M, r["iterations"]
 
 
 def make_dataset(ctx: hf.Context, n_clusters: int, config: int = inputs.CONFIG_GUESS_TRAIN, lo: int = 2, hi: int = 8,
-                 tau: float = 1e-10, prim_tau: float = 1e-14, log=None):
-    Xs, Ts, Ms = [], [], []
+                 tau: float = inputs.BENCH_SCHWARZ_TAU, prim_tau: float = inputs.BENCH_PRIM_TAU, log=None,
+                 workers: int = 1):
+    """Features and plain-SCF density targets of clusters m = 0..n_clusters-1 (seeds (config, m)).  With
+    workers > 1, that many host threads each drive their own context and CUDA stream, so that the small
+    clusters' SCFs overlap on the GPU; the result does not depend on the number of workers."""
     t0 = time.perf_counter()
-    iters = []
-    for m in range(n_clusters):
-        geom = inputs.batch_cluster(config, m, lo, hi)
-        basis = inputs.synthetic_basis(geom)
-        s = hf.System(ctx, geom, basis, schwarz_tau=tau, prim_tau=prim_tau)
-        r = hf.scf(s, e_tol=1e-9, d_tol=1e-6)
-        X, meta = hf.guess_features(s)
-        T, M = pair_targets(r["P"], meta)
-        Xs.append(X)
-        Ts.append(T)
-        Ms.append(M)
-        iters.append(r["iterations"])
-        s.close()
-        if log and (m + 1) % 100 == 0:
-            log(f"dataset: {m + 1}/{n_clusters} clusters, {time.perf_counter() - t0:.1f} s")
-    return {"X": np.concatenate(Xs), "T": np.concatenate(Ts), "M": np.concatenate(Ms),
-            "seconds": time.perf_counter() - t0, "clusters": n_clusters, "scf_iterations": iters}
+    out = [None] * n_clusters
+    if workers <= 1:
+        for m in range(n_clusters):
+            out[m] = _cluster_sample(ctx, config, m, lo, hi, tau, prim_tau)
+            if log and (m + 1) % 100 == 0:
+                log(f"dataset: {m + 1}/{n_clusters} clusters, {time.perf_counter() - t0:.1f} s")
+    else:
+        import torch
+        dev = ctx.device
+        lock = threading.Lock()
+        nxt = [0]
+        errors = []
+
+        def run():
+            try:
+                stream = torch.cuda.Stream(device=dev)
+                wctx = hf.Context(dev, stream)
+                while True:
+                    with lock:
+                        m = nxt[0]
+                        nxt[0] += 1
+                    if m >= n_clusters:
+                        break
+                    out[m] = _cluster_sample(wctx, config, m, lo, hi, tau, prim_tau)
+                    if log and (m + 1) % 100 == 0:
+                        log(f"dataset: {m + 1}/{n_clusters} clusters, {time.perf_counter() - t0:.1f} s")
+                wctx.close()
+            except Exception as e:  # reported after the join
+                errors.append(e)
+
+        threads = [threading.Thread(target=run) for _ in range(workers)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errors:
+            raise errors[0]
+    return {"X": np.concatenate([o[0] for o in out]), "T": np.concatenate([o[1] for o in out]),
+            "M": np.concatenate([o[2] for o in out]), "seconds": time.perf_counter() - t0, "clusters": n_clusters,
+            "scf_iterations": [o[3] for o in out]}
 
 
 def train(model: hf.Model, data: dict, steps: int = 3000, batch: int = 2048, lr: float = 1e-3, seed: int = 0,
           log=None) -> list:
+    """hf_guess_train over the whole dataset (moved to the device once); returns the minibatch losses."""
     import torch
     dev = torch.device("cuda", model.ctx.device)
     X = torch.from_numpy(data["X"]).to(dev)
     T = torch.from_numpy(data["T"]).to(dev)
     M = torch.from_numpy(data["M"]).to(dev)
-    n = X.shape[0]
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    losses = []
-    for k in range(steps):
-        idx = torch.randint(0, n, (min(batch, n),), generator=g).to(dev)
-        xb, tb, mb = X[idx].contiguous(), T[idx].contiguous(), M[idx].contiguous()
-        lr_k = lr * 0.5 * (1.0 + np.cos(np.pi * k / steps))  # cosine decay
-        losses.append(model.train_step(xb, tb, mb, lr_k))
-        if log and (k + 1) % 500 == 0:
-            log(f"train: step {k + 1}/{steps} loss {np.mean(losses[-100:]):.5f}")
-    return losses
+    losses = hf.guess_train(model, X, T, M, steps=steps, batch=batch, lr=lr, seed=seed)
+    if log:
+        log(f"train: {steps} steps, loss {float(losses[:10].mean()):.5f} -> {float(losses[-100:].mean()):.5f}")
+    return [float(x) for x in losses]
 
 
 def predict_or_none(model: hf.Model, system: hf.System):
@@ -101,7 +126,8 @@ def predict_or_none(model: hf.Model, system: hf.System):
 
 
 def evaluate(ctx: hf.Context, model: hf.Model, n_eval: int = 32, waters: int = 32,
-             config: int = inputs.CONFIG_GUESS_EVAL, tau: float = 1e-10, prim_tau: float = 1e-14,
+             config: int = inputs.CONFIG_GUESS_EVAL, tau: float = inputs.BENCH_SCHWARZ_TAU,
+             prim_tau: float = inputs.BENCH_PRIM_TAU,
              fp32_cutoff: float = 1e-4, log=None) -> dict:
     """Per held-out cluster, three SCFs to the same convergence test (|dE| < 1e-9, RMS dP < 1e-6):
     plain FP64 from the core-Hamiltonian guess, FP64 from the learned guess, and mixed precision

@@ -7,6 +7,7 @@ PyTorch supplies device memory and the CUDA stream.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import sys
 
@@ -109,6 +110,11 @@ class BatchInfo_c(ctypes.Structure):
 HF_BATCH_SEQUENTIAL = 4
 
 
+class TrainOpts_c(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("pad", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
 class HFError(RuntimeError):
     def __init__(self, code, where, msg):
         super().__init__(f"{where}: status {code} ({msg})")
@@ -170,6 +176,9 @@ def load_library():
                                         ctypes.c_int]
     lib.hf_guess_features.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.hf_guess_predict.argtypes = [vp, vp, vp, ctypes.c_int]
+    lib.hf_guess_targets.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    lib.hf_guess_train.argtypes = [vp, ctypes.c_int64, vp, vp, vp, ctypes.POINTER(TrainOpts_c), vp, ctypes.c_int]
+    lib.hf_fock_assemble.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     _lib = lib
     return lib
 
@@ -344,7 +353,7 @@ class Batch:
         off = (ctypes.c_int64 * (n + 1))()
         _check(load_library().hf_batch_offsets(self._h, off), "hf_batch_offsets")
         self.offsets = np.array(list(off), dtype=np.int64)
-        self.n_bf = [int(np.sqrt(self.offsets[m + 1] - self.offsets[m]) + 0.5) for m in range(n)]
+        self.n_bf = [math.isqrt(int(self.offsets[m + 1] - self.offsets[m])) for m in range(n)]  # blocks are N_m^2
 
     def info(self) -> dict:
         inf = BatchInfo_c()
@@ -507,28 +516,100 @@ def fock_build_noalloc(system: "System", P, F, J=None, K=None):
     return F
 
 
+def _is_dev(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
 def fock_build_partial(system: "System", P, shard: int = 0, n_shards: int = 1, density_screen: bool = False,
-                       fp64_only: bool = False):
-    """hf_fock_build_partial on host arrays: (J_shard, K_shard).  density_screen also skips quartets whose
-    Schwarz bound times the largest |P| of the six blocks they touch is below the Schwarz threshold."""
+                       fp64_only: bool = False, J=None, K=None):
+    """hf_fock_build_partial: (J_shard, K_shard).  ``P`` is a numpy array (host path) or a contiguous float64
+    CUDA tensor (device path, outputs are CUDA tensors).  density_screen also skips quartets whose Schwarz
+    bound times the largest |P| of the six blocks they touch is below the Schwarz threshold."""
     N = system.n_bf
+    flags = (HF_DENSITY_SCREEN if density_screen else 0) | (HF_FP64_ONLY if fp64_only else 0)
+    if _is_dev(P):
+        torch = _torch()
+        if P.dtype != torch.float64 or not P.is_contiguous() or tuple(P.shape) != (N, N):
+            raise ValueError("P must be a contiguous float64 N x N CUDA tensor")
+        J = torch.empty_like(P) if J is None else J
+        K = torch.empty_like(P) if K is None else K
+        _check(load_library().hf_fock_build_partial(system._h, P.data_ptr(), int(shard), int(n_shards), J.data_ptr(),
+                                                    K.data_ptr(), flags | HF_PTR_DEVICE), "hf_fock_build_partial")
+        return J, K
     P = _as_f64(P)
-    J, K = np.empty((N, N)), np.empty((N, N))
-    flags = HF_PTR_HOST | (HF_DENSITY_SCREEN if density_screen else 0) | (HF_FP64_ONLY if fp64_only else 0)
+    J = np.empty((N, N)) if J is None else J
+    K = np.empty((N, N)) if K is None else K
     _check(load_library().hf_fock_build_partial(system._h, P.ctypes.data, int(shard), int(n_shards), J.ctypes.data,
-                                                K.ctypes.data, flags), "hf_fock_build_partial")
+                                                K.ctypes.data, flags | HF_PTR_HOST), "hf_fock_build_partial")
     return J, K
 
 
-def assemble_shards(H, J_part, K_part, all_reduce_sum):
-    """F = H + sum_r J_r - 1/2 sum_r K_r from this rank's partial J and K.
+def fock_assemble(system: "System", J, K, P=None, energy: bool = False):
+    """hf_fock_assemble: F = H + J - K/2 (and E_elec from P) from J and K summed over every shard.
+    Host arrays or CUDA tensors (all of one kind).  Returns (F, E_elec or None)."""
+    N = system.n_bf
+    e = ctypes.c_double(0.0)
+    if energy and P is None:
+        raise ValueError("the energy needs the density P")
+    if _is_dev(J):
+        torch = _torch()
+        F = torch.empty_like(J)
+        _check(load_library().hf_fock_assemble(system._h, P.data_ptr() if P is not None else None, J.data_ptr(),
+                                               K.data_ptr(), F.data_ptr(), ctypes.byref(e) if energy else None,
+                                               HF_PTR_DEVICE), "hf_fock_assemble")
+    else:
+        J, K = _as_f64(J), _as_f64(K)
+        Pp = _as_f64(P) if P is not None else None
+        F = np.empty((N, N))
+        _check(load_library().hf_fock_assemble(system._h, Pp.ctypes.data if Pp is not None else None, J.ctypes.data,
+                                               K.ctypes.data, F.ctypes.data, ctypes.byref(e) if energy else None,
+                                               HF_PTR_HOST), "hf_fock_assemble")
+    return F, (e.value if energy else None)
 
-    ``all_reduce_sum`` sums an array over the ranks (for example an NCCL or
-    gloo allreduce); this is the reduction the paper performs with ddi_gsumf.
-    Returns (F, J, K)."""
+
+def assemble_shards(system: "System", J_part, K_part, all_reduce_sum, P=None, energy: bool = False,
+                    assemble=None):
+    """F of a sharded build from this rank's partial J and K.
+
+    ``all_reduce_sum`` returns the sum of an array or tensor over the ranks
+    (for example an NCCL or gloo allreduce): the reduction the paper performs
+    with ddi_gsumf.  ``assemble`` (default: the library's hf_fock_assemble)
+    then forms F (and E_elec from P).  Returns (F, J, K, E_elec or None)."""
     J = all_reduce_sum(J_part)
     K = all_reduce_sum(K_part)
-    return H + J - 0.5 * K, J, K
+    F, E = (assemble or fock_assemble)(system, J, K, P=P, energy=energy)
+    return F, J, K, E
+
+
+def sharded_fock_build(system: "System", P, rank: int, world: int, all_reduce_sum, energy: bool = True,
+                       build_partial=None, assemble=None):
+    """One rank's part of a Fock build sharded over ``world`` ranks (Algorithms 2/3 with ddi_gsumf): the
+    quartet shard ``rank`` of every class (hf_fock_build_partial), one sum of J and one of K over the ranks,
+    and the assembly of F.  Every rank returns the full (F, J, K, E_elec).  ``build_partial`` and
+    ``assemble`` default to the library calls."""
+    J, K = (build_partial or fock_build_partial)(system, P, rank, world)
+    return assemble_shards(system, J, K, all_reduce_sum, P=P, energy=energy, assemble=assemble)
+
+
+def guess_targets(system: "System", P):
+    """hf_guess_targets on a host density: T and mask [n_pairs, 325] float32 host arrays."""
+    n = ctypes.c_int64(0)
+    _check(load_library().hf_guess_features(system._h, None, None, ctypes.byref(n), 0), "hf_guess_features")
+    P = _as_f64(P)
+    T = np.empty((n.value, Model.N_OUT), dtype=np.float32)
+    M = np.empty((n.value, Model.N_OUT), dtype=np.float32)
+    _check(load_library().hf_guess_targets(system._h, P.ctypes.data, T.ctypes.data, M.ctypes.data, HF_PTR_HOST),
+           "hf_guess_targets")
+    return T, M
+
+
+def guess_train(model: "Model", X, T, mask, steps: int, batch: int = 2048, lr: float = 1e-3, seed: int = 0):
+    """hf_guess_train on a dataset in CUDA float32 tensors; returns the per-step minibatch losses."""
+    losses = np.zeros(int(steps), dtype=np.float32)
+    o = TrainOpts_c(int(steps), int(batch), float(lr), 0, int(seed))
+    _check(load_library().hf_guess_train(model._h, int(X.shape[0]), X.data_ptr(), T.data_ptr(), mask.data_ptr(),
+                                         ctypes.byref(o), losses.ctypes.data, HF_PTR_DEVICE), "hf_guess_train")
+    return losses
 
 
 def stats_dict(st: Stats_c) -> dict:

@@ -63,6 +63,11 @@ CONFIG_BATCH = 4            # 512 molecules of 1..16 waters
 CONFIG_GUESS_TRAIN = 5      # learned-guess training clusters
 CONFIG_GUESS_EVAL = 6       # learned-guess held-out clusters
 
+# Thresholds of the benchmarked workloads: Schwarz screening of shell quartets and the primitive-pair
+# threshold (a primitive quartet is skipped when the product of its two primitive-pair bounds is below it).
+BENCH_SCHWARZ_TAU = 1e-10
+BENCH_PRIM_TAU = 1e-14
+
 
 @dataclass
 class Geometry:
@@ -199,6 +204,18 @@ def random_orbitals(n_bf: int, n_occ: int, config_id: int, index: int = 0) -> np
     """G ~ N(0,1), shape [n_bf, n_occ]; orthonormalisation is left to the caller."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(config_id), int(index), 1])))
     return rng.standard_normal((n_bf, n_occ))
+
+
+def guess_init_weights(seed: int = 0) -> np.ndarray:
+    """Seeded initial weights of the learned-guess MLP (float32, in the library's layout W1[256][16], b1,
+    W2[256][256], b2, W3[325][256], b3): He-uniform matrices (the output layer scaled by 0.1), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((16, 256), (256, 256), (256, 325)):
+        lim = math.sqrt(6.0 / fan_in) * (1.0 if fan_out != 325 else 0.1)
+        parts.append(rng.uniform(-lim, lim, size=(fan_out, fan_in)).astype(np.float32).ravel())
+        parts.append(np.zeros(fan_out, dtype=np.float32))
+    return np.concatenate(parts)
 
 
 def n_electrons(geom: Geometry) -> int:

@@ -66,3 +66,31 @@ def test_product_does_not_use_the_oracle():
                     if pat.search(fh.read()):
                         hits.append(f)
     assert not hits, hits
+
+
+def test_binding_holds_no_method_arithmetic():
+    """The Python layer only marshals: the binding and the learned-guess driver contain no matrix products
+    and no numerical functions applied to the method's data (Fock assembly, density blocks, learning-rate
+    schedules and training steps all run in the library).  Checked on their syntax trees."""
+    import ast
+    import paper_1708_00033_gb300 as pkg
+    root = os.path.dirname(pkg.__file__)
+    banned_calls = {"cos", "sin", "exp", "log", "sqrt", "einsum", "dot", "matmul", "tensordot", "trace", "outer",
+                    "eigh", "solve", "cholesky", "inv", "tanh"}
+    for name in ("hf.py", "guess.py"):
+        tree = ast.parse(open(os.path.join(root, name)).read())
+        for node in ast.walk(tree):
+            assert not (isinstance(node, ast.BinOp) and isinstance(node.op, ast.MatMult)), (name, node.lineno)
+            if isinstance(node, ast.Call) and isinstance(node.func, ast.Attribute):
+                f = node.func
+                base = f.value.id if isinstance(f.value, ast.Name) else (
+                    f.value.attr if isinstance(f.value, ast.Attribute) else "")
+                if base in ("np", "numpy", "math", "torch", "linalg"):
+                    assert f.attr not in banned_calls, (name, node.lineno, f.attr)
+            # no arithmetic that combines two matrices (X + Y, X - c * Y, ...): binary +/-/* whose operands
+            # are both names, subscripts or calls
+            if isinstance(node, ast.BinOp) and isinstance(node.op, (ast.Add, ast.Sub, ast.Mult)):
+                kinds = (ast.Name, ast.Subscript, ast.Call, ast.BinOp)
+                if isinstance(node.left, kinds) and isinstance(node.right, kinds):
+                    names = {n.id for n in ast.walk(node) if isinstance(n, ast.Name)}
+                    assert not names & {"H", "J", "K", "F", "P", "S", "C"}, (name, node.lineno)

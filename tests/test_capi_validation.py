@@ -128,6 +128,9 @@ def test_null_handles_are_rejected():
         "hf_model_train_step": lambda: lib.hf_model_train_step(n, 1, p, p, p, 1e-3, None, 0),
         "hf_guess_features": lambda: lib.hf_guess_features(n, n, n, None, 0),
         "hf_guess_predict": lambda: lib.hf_guess_predict(n, n, n, 0),
+        "hf_guess_targets": lambda: lib.hf_guess_targets(n, p, p, p, 0),
+        "hf_guess_train": lambda: lib.hf_guess_train(n, 1, p, p, p, None, None, 1),
+        "hf_fock_assemble": lambda: lib.hf_fock_assemble(n, p, p, p, p, None, 0),
     }
     for name, call in calls.items():
         assert call() == hf.HF_E_INVALID, name

@@ -132,6 +132,29 @@ def test_invalid_density_is_rejected(ctx, oracle_mod):
     assert np.isfinite(out["F"]).all()
 
 
+def test_invalid_density_device_path_leaves_outputs(ctx):
+    """The density check runs on the device and the host reads it once, after the build: a rejected density
+    still returns HF_E_INVALID and every device output keeps its previous contents."""
+    import torch
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(2, 1, 4)
+    basis = I.synthetic_basis(geom)
+    s = hf.System(ctx, geom, basis, schwarz_tau=1e-10)
+    N = s.n_bf
+    P = torch.eye(N, dtype=torch.float64, device="cuda")
+    P[0, 3] = 0.25  # not symmetric
+    F, J, K = (torch.full_like(P, 7.0) for _ in range(3))
+    with pytest.raises(hf.HFError) as e:
+        s.fock_build(P, F=F, J=J, K=K)
+    assert e.value.code == hf.HF_E_INVALID
+    for t in (F, J, K):
+        assert bool((t == 7.0).all())
+    P[0, 3] = 0.0
+    out = s.fock_build(P, F=F, J=J, K=K, want_J=True, want_K=True)
+    ref = s.fock_build(P.cpu().numpy(), want_J=True, want_K=True)
+    assert float(np.abs(out["F"].cpu().numpy() - ref["F"]).max()) <= 1e-13
+
+
 def test_unsupported_basis_is_rejected(ctx):
     from paper_1708_00033_gb300 import hf
     geom = I.water_cluster(1, 1, 1)
@@ -174,13 +197,41 @@ def test_shards_sum_to_full_build(ctx, oracle_mod, n_shards):
     s = hf.System(ctx, geom, basis, schwarz_tau=1e-10, prim_tau=1e-14)
     full = s.fock_build(P, want_J=True, want_K=True)
     parts = [hf.fock_build_partial(s, P, k, n_shards) for k in range(n_shards)]
-    S_, H = s.one_electron()
     # stand-in for an allreduce over ranks: shard 0's partial matrices summed with the others
     sums = {id(parts[0][0]): sum(p[0] for p in parts), id(parts[0][1]): sum(p[1] for p in parts)}
-    F, J, K = hf.assemble_shards(H, parts[0][0], parts[0][1], lambda a: sums[id(a)])
+    F, J, K, E = hf.assemble_shards(s, parts[0][0], parts[0][1], lambda a: sums[id(a)], P=P, energy=True)
     assert np.abs(J - full["J"]).max() <= 1e-12
     assert np.abs(K - full["K"]).max() <= 1e-12
     assert np.abs(F - full["F"]).max() <= 1e-12
+    assert abs(E - full["E_elec"]) <= 1e-10
+    # the same through device tensors (the path an NCCL allreduce uses)
+    import torch
+    Pd = torch.from_numpy(P).cuda()
+    dparts = [hf.fock_build_partial(s, Pd, k, n_shards) for k in range(n_shards)]
+    for (Jh, Kh), (Jd, Kd) in zip(parts, dparts):
+        assert float(np.abs(Jd.cpu().numpy() - Jh).max()) <= 1e-13
+        assert float(np.abs(Kd.cpu().numpy() - Kh).max()) <= 1e-13
+    dsum = {id(dparts[0][0]): sum(p[0] for p in dparts), id(dparts[0][1]): sum(p[1] for p in dparts)}
+    Fd, _, _, Ed = hf.sharded_fock_build(s, Pd, 0, n_shards, lambda a: dsum[id(a)],
+                                         build_partial=lambda *a_: dparts[0])
+    assert float((Fd - torch.from_numpy(full["F"]).cuda()).abs().max()) <= 1e-12
+    assert abs(Ed - full["E_elec"]) <= 1e-10
+
+
+def test_fock_assemble_rejects_non_finite(ctx):
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(1, 1, 1)
+    basis = I.synthetic_basis(geom)
+    s = hf.System(ctx, geom, basis)
+    N = s.n_bf
+    J, K = np.eye(N), np.eye(N)
+    F, _ = hf.fock_assemble(s, J, K)
+    _, H = s.one_electron()
+    assert np.abs(F - (H + 0.5 * np.eye(N))).max() == 0.0
+    K[3, 4] = np.inf
+    with pytest.raises(hf.HFError) as e:
+        hf.fock_assemble(s, J, K)
+    assert e.value.code == hf.HF_E_INVALID
 
 
 @pytest.mark.parametrize("eps,prim_tau", [(1e-3, 0.0), (1e-6, 0.0), (1e-6, 1e-14)])
@@ -192,10 +243,14 @@ def test_density_screened_difference_build(ctx, oracle_mod, eps, prim_tau):
     build of dP.  A skipped quartet changes a J element by less than tau and a
     K element by less than tau/2, a skipped primitive quartet by less than
     4 prim_tau (at most 81 per quartet here), and at most 2 n_pairs quartets
-    touch a J element and 4 n_sh^2 a K element: that is the tolerance."""
+    touch a J element and 4 n_sh^2 a K element: that is the tolerance.
+    Per skipped quartet: 4 f X P < tau for J (4 Q_ab Q_cd max|dP| < tau), and
+    2 f X P < tau/2 for K; per skipped primitive quartet 4 prim_tau (J) and
+    2 prim_tau (K)."""
     from paper_1708_00033_gb300 import hf
     tau = 1e-10
-    per_quartet = tau + 81 * 4 * prim_tau
+    per_quartet_J = tau + 81 * 4 * prim_tau
+    per_quartet_K = 0.5 * tau + 81 * 2 * prim_tau
     geom = I.water_cluster(4, I.CONFIG_SINGLE_BUILD)
     basis = I.synthetic_basis(geom)
     mol = oracle_mod.Molecule(geom, basis)
@@ -210,8 +265,8 @@ def test_density_screened_difference_build(ctx, oracle_mod, eps, prim_tau):
     J, K = hf.fock_build_partial(s, dP, density_screen=True, fp64_only=True)
     n_sh = basis.n_shells
     n_pairs = n_sh * (n_sh + 1) // 2
-    assert np.abs(J - J_ref).max() <= 2 * n_pairs * per_quartet
-    assert np.abs(K - K_ref).max() <= 4 * n_sh * n_sh * per_quartet
+    assert np.abs(J - J_ref).max() <= 2 * n_pairs * per_quartet_J
+    assert np.abs(K - K_ref).max() <= 4 * n_sh * n_sh * per_quartet_K
     if prim_tau == 0.0:
         # the same call without the density test is the plain Schwarz-screened build
         J2, K2 = hf.fock_build_partial(s, dP, fp64_only=True)

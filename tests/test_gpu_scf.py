@@ -51,6 +51,20 @@ def test_scf_h2_textbook(ctx, oracle_mod):
     assert abs(r["energy"] - (-1.1167)) <= 0.5e-4
 
 
+_ORACLE_SCF = {}
+
+
+def _oracle_scf(oracle_mod, nw, seed):
+    """The oracle's unscreened SCF of a cluster, converged tightly (cached per cluster)."""
+    if (nw, seed) not in _ORACLE_SCF:
+        geom = I.water_cluster(nw, 2, seed)
+        basis = I.synthetic_basis(geom)
+        ref = oracle_mod.scf(oracle_mod.Molecule(geom, basis), e_tol=1e-11, d_tol=1e-8)
+        assert ref.converged
+        _ORACLE_SCF[(nw, seed)] = ref
+    return _ORACLE_SCF[(nw, seed)]
+
+
 @pytest.mark.parametrize("nw,seed", [(1, 2), (2, 4)])
 def test_scf_vs_oracle(ctx, oracle_mod, nw, seed):
     from paper_1708_00033_gb300 import hf
@@ -58,11 +72,46 @@ def test_scf_vs_oracle(ctx, oracle_mod, nw, seed):
     basis = I.synthetic_basis(geom)
     s = hf.System(ctx, geom, basis)
     r = hf.scf(s, e_tol=1e-11, d_tol=1e-8)
-    ref = oracle_mod.scf(oracle_mod.Molecule(geom, basis), e_tol=1e-11, d_tol=1e-8)
-    assert r["converged"] and ref.converged
+    ref = _oracle_scf(oracle_mod, nw, seed)
+    assert r["converged"]
     assert abs(r["energy"] - ref.energy) < 1e-9
     assert np.abs(r["P"] - ref.P).max() < 1e-6
     assert np.abs(r["eps"][: len(ref.eps)] - ref.eps).max() < 1e-6
+
+
+@pytest.mark.parametrize("nw,seed", [(2, 4), (3, 6)])
+def test_mixed_scf_vs_oracle(ctx, oracle_mod, nw, seed):
+    """Mixed-then-FP64 SCF (FP32 integrals for Q_ij Q_kl < 1e-4 until |dE| < 1e-5, FP64 builds from
+    then on, convergence declared on FP64 builds only) from the core-Hamiltonian guess: its energy is the
+    plain method's, within 1e-8 Eh of the oracle's SCF and 1e-9 of the plain GPU SCF."""
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(nw, 2, seed)
+    basis = I.synthetic_basis(geom)
+    plain = hf.scf(hf.System(ctx, geom, basis), e_tol=1e-11, d_tol=1e-8)
+    sm = hf.System(ctx, geom, basis, fp32_cutoff=1e-4)
+    assert sm.info["quartets_fp32"] > 0
+    mixed = hf.scf(sm, e_tol=1e-11, d_tol=1e-8)
+    assert plain["converged"] and mixed["converged"]
+    assert 0 < mixed["mixed_iterations"] < mixed["iterations"]  # the last builds were FP64 only
+    ref = _oracle_scf(oracle_mod, nw, seed)
+    assert abs(mixed["energy"] - ref.energy) <= 1e-8
+    assert abs(mixed["energy"] - plain["energy"]) <= 1e-9
+    assert np.abs(mixed["P"] - plain["P"]).max() < 1e-6
+
+
+def test_mixed_scf_from_a_given_density(ctx):
+    """The mixed phase also runs from a supplied starting density (the learned guess's path): started from
+    a slightly perturbed converged density it still switches to FP64 and lands on the plain energy."""
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(3, 2, 6)
+    basis = I.synthetic_basis(geom)
+    plain = hf.scf(hf.System(ctx, geom, basis), e_tol=1e-11, d_tol=1e-8)
+    rng = np.random.default_rng(2)
+    D = rng.standard_normal(plain["P"].shape) * 1e-2
+    Pg = plain["P"] + 0.5 * (D + D.T)
+    mixed = hf.scf(hf.System(ctx, geom, basis, fp32_cutoff=1e-4), e_tol=1e-11, d_tol=1e-8, P_guess=Pg)
+    assert mixed["converged"] and 0 < mixed["mixed_iterations"] < mixed["iterations"]
+    assert abs(mixed["energy"] - plain["energy"]) <= 1e-9
 
 
 def test_scf_invariants_sixteen_waters(ctx):

@@ -1,6 +1,8 @@
 """Multi-rank host logic on CPU with two gloo ranks: the bench's
-max-over-ranks timing reduction and the assembly of a sharded Fock matrix from
-per-rank partial J and K (the paper's ddi_gsumf step)."""
+max-over-ranks timing reduction and the sharded Fock build's rank logic
+(each rank's shard, one sum of J and one of K over the ranks - the paper's
+ddi_gsumf step - and the assembly).  The library calls are replaced by
+stand-ins here (no GPU); the GPU tests check the same calls on the device."""
 import os
 import socket
 
@@ -18,26 +20,38 @@ def _free_port():
     return port
 
 
+N = 12
+
+
+def _partial_stand_in(system, P, shard, n_shards):
+    """Deterministic per-shard matrices standing in for hf_fock_build_partial."""
+    rng = np.random.default_rng(100 + shard + 10 * n_shards)
+    return rng.standard_normal((N, N)), rng.standard_normal((N, N))
+
+
+def _assemble_stand_in(system, J, K, P=None, energy=False):
+    F = np.eye(N) + J - 0.5 * K
+    return F, (float(np.sum(P * (np.eye(N) + F))) / 2 if energy else None)
+
+
 def _worker(rank, world, port, out_dir):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    from paper_1708_00033_gb300.hf import assemble_shards
+    from paper_1708_00033_gb300 import hf
     m = bench.reduce_max(10.0 + 5.0 * rank, dist, torch.device("cpu"))
-    rng = np.random.default_rng(100 + rank)
-    N = 12
-    Jp, Kp = rng.standard_normal((N, N)), rng.standard_normal((N, N))
-    H = np.eye(N)
 
     def allsum(a):
         t = torch.from_numpy(np.array(a, copy=True))
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return t.numpy()
 
-    F, J, K = assemble_shards(H, Jp, Kp, allsum)
-    np.savez(os.path.join(out_dir, f"rank{rank}.npz"), m=m, F=F, J=J, K=K, Jp=Jp, Kp=Kp)
+    P = np.full((N, N), 0.1)
+    F, J, K, E = hf.sharded_fock_build(None, P, rank, world, allsum, energy=True, build_partial=_partial_stand_in,
+                                       assemble=_assemble_stand_in)
+    np.savez(os.path.join(out_dir, f"rank{rank}.npz"), m=m, F=F, J=J, K=K, E=E)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -48,8 +62,10 @@ def test_two_gloo_ranks(tmp_path):
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     r = [np.load(tmp_path / f"rank{k}.npz") for k in range(world)]
     assert float(r[0]["m"]) == 15.0 and float(r[1]["m"]) == 15.0
-    J = r[0]["Jp"] + r[1]["Jp"]
-    K = r[0]["Kp"] + r[1]["Kp"]
+    parts = [_partial_stand_in(None, None, k, world) for k in range(world)]
+    J = parts[0][0] + parts[1][0]
+    K = parts[0][1] + parts[1][1]
     for k in range(world):
         assert np.allclose(r[k]["J"], J, atol=1e-14) and np.allclose(r[k]["K"], K, atol=1e-14)
-        assert np.allclose(r[k]["F"], np.eye(12) + J - 0.5 * K, atol=1e-14)
+        assert np.allclose(r[k]["F"], np.eye(N) + J - 0.5 * K, atol=1e-14)
+        assert abs(float(r[k]["E"]) - float(r[0]["E"])) == 0.0

@@ -335,3 +335,47 @@ def test_strided_sample_partitions_the_unique_loop(oracle_mod, dimer, tau):
     assert sum(u for _, u in got) == n_p * (n_p + 1) // 2
     if tau == 0.0:
         assert full == n_p * (n_p + 1) // 2
+
+
+def test_shell_blocks_vs_literal(oracle_mod):
+    """Whole J/K shell blocks by definition equal the literal ordered-index sums (themselves pinned to
+    numpy einsum above), on every shell pair of one water."""
+    g = I.water_cluster(1, 1, 3)
+    b = I.synthetic_basis(g)
+    m = oracle_mod.Molecule(g, b)
+    S, _ = m.core_hamiltonian()
+    P = oracle_mod.density_from_orbitals(oracle_mod.orthonormalise(I.random_orbitals(m.n_bf, 5, 1, 3), S))
+    Jl, Kl = m.jk_literal(P)
+    blocks = [(i, j) for i in range(m.n_shells) for j in range(m.n_shells)]
+    Jb, Kb = m.jk_shell_blocks(P, blocks)
+    for (i, j), jb, kb in zip(blocks, Jb, Kb):
+        r, c = int(m.bf0[i]), int(m.bf0[j])
+        assert np.abs(jb - Jl[r:r + jb.shape[0], c:c + jb.shape[1]]).max() < 1e-12
+        assert np.abs(kb - Kl[r:r + kb.shape[0], c:c + kb.shape[1]]).max() < 1e-12
+
+
+def test_screened_elements_and_blocks_vs_unique(oracle_mod):
+    """With Schwarz screening, the by-definition elements and shell blocks leave out exactly the integrals
+    the unique-quartet build leaves out: the Coulomb integral (mu nu|lam sig) by Q_IJ Q_kl and the exchange
+    integral (mu lam|nu sig) by Q_Ik Q_Jl.  A threshold large enough to change J and K makes a wrong pair
+    index visible."""
+    g = I.water_cluster(3, 2, 5)
+    b = I.synthetic_basis(g)
+    m = oracle_mod.Molecule(g, b)
+    S, _ = m.core_hamiltonian()
+    P = oracle_mod.density_from_orbitals(oracle_mod.orthonormalise(I.random_orbitals(m.n_bf, 15, 2, 5), S))
+    tau = 1e-6
+    J0, K0 = m.jk_unique(P)
+    Ju, Ku = m.jk_unique(P, tau)
+    assert np.abs(Ju - J0).max() > 1e-8 and np.abs(Ku - K0).max() > 1e-8  # the threshold matters here
+    rng = np.random.default_rng(11)
+    blocks = [(int(x), int(y)) for x, y in rng.integers(0, m.n_shells, size=(16, 2))] + [(0, 0), (5, 5)]
+    Jb, Kb = m.jk_shell_blocks(P, blocks, tau=tau)
+    for (i, j), jb, kb in zip(blocks, Jb, Kb):
+        r, c = int(m.bf0[i]), int(m.bf0[j])
+        assert np.abs(jb - Ju[r:r + jb.shape[0], c:c + jb.shape[1]]).max() < 1e-12
+        assert np.abs(kb - Ku[r:r + kb.shape[0], c:c + kb.shape[1]]).max() < 1e-12
+    pairs = [(int(x), int(y)) for x, y in rng.integers(0, m.n_bf, size=(12, 2))]
+    Je, Ke = m.jk_elements(P, pairs, tau=tau)
+    for t, (mu, nu) in enumerate(pairs):
+        assert abs(Je[t] - Ju[mu, nu]) < 1e-12 and abs(Ke[t] - Ku[mu, nu]) < 1e-12
