@@ -67,9 +67,14 @@ typedef struct {
 } hf_geometry;
 
 /* Contracted Cartesian shells (Section 4.1's "shell": functions on one atom
- * sharing exponents).  atom[s] atom index, l[s] in 0..2, nprim[s] in 1..8,
- * exps/coefs: sum(nprim) primitive exponents and coefficients, shell after
- * shell.  Host memory. */
+ * sharing exponents).  atom[s] atom index, l[s] in 0..2 or HF_SP_SHELL,
+ * nprim[s] in 1..8, exps/coefs: sum(nprim) primitive exponents and
+ * coefficients, shell after shell.  An sp (L) shell, as in split-valence
+ * bases such as 6-31G(d) (the paper's basis, Section 5), is an s and a p
+ * shell sharing exponents: coefs holds its s coefficients and coefs_p its p
+ * coefficients (coefs_p is read only at sp shells and may be NULL when there
+ * are none); its functions are ordered s, x, y, z.  Host memory. */
+#define HF_SP_SHELL -1
 typedef struct {
     int32_t n_shells;
     const int32_t* atom;
@@ -77,6 +82,7 @@ typedef struct {
     const int32_t* nprim;
     const double* exps;
     const double* coefs;
+    const double* coefs_p;
 } hf_basis;
 
 /* Screening and precision thresholds.
@@ -163,8 +169,10 @@ const char* hf_last_error(void);
  * by angular class and bound, and the per-class quartet schedule for the
  * given thresholds.  Geometry and basis are read from host memory and not
  * kept.  Errors: HF_E_INVALID (null/negative sizes, atom index out of
- * range, non-positive exponent, NaN, negative threshold), HF_E_UNSUPPORTED
- * (l > 2, nprim > 8), HF_E_NOMEM, HF_E_CUDA. */
+ * range, non-positive exponent, NaN, negative threshold, sp shell without
+ * coefs_p), HF_E_UNSUPPORTED (l > 2, nprim > 8), HF_E_NOMEM, HF_E_CUDA.
+ * The system holds an sp shell as an s shell followed by a p shell with the
+ * same exponents, so hf_system_info counts both. */
 int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis, const hf_thresholds* th,
                      hf_system** sys);
 

@@ -123,18 +123,48 @@ def one_electron_primitive(pa, a, A, pb, b, B, Zc, C):
     return out
 
 
+def _split_sp(basis):
+    """Shell lists with every sp (L) shell (l = -1) written as its s shell (coefficients coefs) followed by
+    its p shell (coefficients coefs_p), both with the sp shell's exponents: an sp shell is by definition
+    those two shells sharing exponents, with functions s, x, y, z."""
+    l_in = np.asarray(basis.l)
+    if not np.any(l_in == -1):
+        return basis.atom, basis.l, basis.nprim, basis.exps, basis.coefs
+    atom, l, nprim, exps, coefs = [], [], [], [], []
+    o = 0
+    for s_ in range(l_in.size):
+        n = int(basis.nprim[s_])
+        e = list(basis.exps[o:o + n])
+        if l_in[s_] == -1:
+            for lq, c in ((0, basis.coefs), (1, basis.coefs_p)):
+                atom.append(int(basis.atom[s_]))
+                l.append(lq)
+                nprim.append(n)
+                exps += e
+                coefs += list(c[o:o + n])
+        else:
+            atom.append(int(basis.atom[s_]))
+            l.append(int(l_in[s_]))
+            nprim.append(n)
+            exps += e
+            coefs += list(basis.coefs[o:o + n])
+        o += n
+    return atom, l, nprim, exps, coefs
+
+
 class Molecule:
-    """A geometry + basis handle on the oracle side."""
+    """A geometry + basis handle on the oracle side (sp shells are split into s and p shells)."""
 
     def __init__(self, geom, basis):
         lib = _load()
         self.Z = np.ascontiguousarray(geom.Z, dtype=np.int32)
         self.xyz = np.ascontiguousarray(geom.xyz, dtype=np.float64)
-        self._atom = np.ascontiguousarray(basis.atom, dtype=np.int32)
-        self._l = np.ascontiguousarray(basis.l, dtype=np.int32)
-        self._nprim = np.ascontiguousarray(basis.nprim, dtype=np.int32)
-        self._exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
-        self._coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
+        atom, l, nprim, exps, coefs = _split_sp(basis)
+        self._atom = np.ascontiguousarray(atom, dtype=np.int32)
+        self._l = np.ascontiguousarray(l, dtype=np.int32)
+        self._nprim = np.ascontiguousarray(nprim, dtype=np.int32)
+        self._exps = np.ascontiguousarray(exps, dtype=np.float64)
+        self._coefs = np.ascontiguousarray(coefs, dtype=np.float64)
         self.n_shells = int(self._l.shape[0])
         h = lib.or_create(int(self.Z.shape[0]), _i(self.Z), _d(self.xyz), self.n_shells, _i(self._atom),
                           _i(self._l), _i(self._nprim), _d(self._exps), _d(self._coefs))

@@ -481,7 +481,9 @@ static int check_geometry_basis(const hf_geometry* g, const hf_basis* b, const h
     long long np = 0;
     for (int s = 0; s < b->n_shells; s++) {
         if (b->atom[s] < 0 || b->atom[s] >= g->n_atoms) return fail(HF_E_INVALID, "basis: atom index out of range");
-        if (b->l[s] < 0) return fail(HF_E_INVALID, "basis: negative angular momentum");
+        if (b->l[s] == HF_SP_SHELL && !b->coefs_p)
+            return fail(HF_E_INVALID, "basis: sp shell without p coefficients (coefs_p is NULL)");
+        if (b->l[s] < 0 && b->l[s] != HF_SP_SHELL) return fail(HF_E_INVALID, "basis: negative angular momentum");
         if (b->l[s] > kMaxL) return fail(HF_E_UNSUPPORTED, "basis: l > 2 is not supported");
         if (b->nprim[s] < 1) return fail(HF_E_INVALID, "basis: shell without primitives");
         if (b->nprim[s] > kMaxPrim) return fail(HF_E_UNSUPPORTED, "basis: more than 8 primitives in a shell");
@@ -491,6 +493,15 @@ static int check_geometry_basis(const hf_geometry* g, const hf_basis* b, const h
         if (!(b->exps[k] > 0.0) || !isfinite(b->exps[k])) return fail(HF_E_INVALID, "basis: exponent not positive");
         if (!isfinite(b->coefs[k])) return fail(HF_E_INVALID, "basis: non-finite coefficient");
     }
+    if (b->coefs_p) {
+        long long o = 0;
+        for (int s = 0; s < b->n_shells; s++) {
+            if (b->l[s] == HF_SP_SHELL)
+                for (int k = 0; k < b->nprim[s]; k++)
+                    if (!isfinite(b->coefs_p[o + k])) return fail(HF_E_INVALID, "basis: non-finite p coefficient");
+            o += b->nprim[s];
+        }
+    }
     if (th) {
         if (!(th->schwarz_tau >= 0.0) || !(th->fp32_cutoff >= 0.0)) return fail(HF_E_INVALID, "thresholds: negative");
         if (!(th->prim_tau >= 0.0)) return fail(HF_E_INVALID, "thresholds: negative prim_tau");
@@ -498,14 +509,56 @@ static int check_geometry_basis(const hf_geometry* g, const hf_basis* b, const h
     return HF_OK;
 }
 
+// A basis with sp shells written as separate shells: each sp shell becomes an s shell (coefficients
+// coefs) followed by a p shell (coefficients coefs_p) with the same exponents on the same atom, which
+// keeps the basis-function order s, x, y, z of the sp shell.
+struct ExpandedBasis {
+    std::vector<int32_t> atom, l, nprim;
+    std::vector<double> exps, coefs;
+    hf_basis view{};
+};
+
+static const hf_basis* expand_sp_shells(const hf_basis* b, ExpandedBasis& e)
+{
+    bool any = false;
+    for (int s = 0; s < b->n_shells; s++) any |= b->l[s] == HF_SP_SHELL;
+    if (!any) return b;
+    long long o = 0;
+    for (int s = 0; s < b->n_shells; s++) {
+        const int n = b->nprim[s];
+        const int parts = b->l[s] == HF_SP_SHELL ? 2 : 1;
+        for (int part = 0; part < parts; part++) {
+            e.atom.push_back(b->atom[s]);
+            e.l.push_back(b->l[s] == HF_SP_SHELL ? part : b->l[s]);
+            e.nprim.push_back(n);
+            const double* c = part == 1 ? b->coefs_p : b->coefs;
+            for (int k = 0; k < n; k++) {
+                e.exps.push_back(b->exps[o + k]);
+                e.coefs.push_back(c[o + k]);
+            }
+        }
+        o += n;
+    }
+    e.view.n_shells = (int32_t)e.l.size();
+    e.view.atom = e.atom.data();
+    e.view.l = e.l.data();
+    e.view.nprim = e.nprim.data();
+    e.view.exps = e.exps.data();
+    e.view.coefs = e.coefs.data();
+    e.view.coefs_p = nullptr;
+    return &e.view;
+}
+
 extern "C" {
 
-int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis, const hf_thresholds* th,
+int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis_in, const hf_thresholds* th,
                      hf_system** out)
 {
     if (!ctx || !out) return fail(HF_E_INVALID, "hf_system_create: NULL ctx or output pointer");
     *out = nullptr;
-    TRY(check_geometry_basis(geom, basis, th));
+    TRY(check_geometry_basis(geom, basis_in, th));
+    ExpandedBasis eb;
+    const hf_basis* basis = expand_sp_shells(basis_in, eb);
     DeviceGuard g(ctx->device);
     hf_system* S = new hf_system();
     S->ctx = ctx;

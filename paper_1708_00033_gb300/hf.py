@@ -51,7 +51,22 @@ class Geometry_c(ctypes.Structure):
 
 class Basis_c(ctypes.Structure):
     _fields_ = [("n_shells", ctypes.c_int32), ("atom", _i32p), ("l", _i32p), ("nprim", _i32p),
-                ("exps", _f64p), ("coefs", _f64p)]
+                ("exps", _f64p), ("coefs", _f64p), ("coefs_p", _f64p)]
+
+
+HF_SP_SHELL = -1
+
+
+def _basis_c(basis, keep: list):
+    """hf_basis of an inputs.Basis; the arrays it points to are appended to ``keep``."""
+    at, l, npr = _as_i32(basis.atom), _as_i32(basis.l), _as_i32(basis.nprim)
+    ex, co = _as_f64(basis.exps), _as_f64(basis.coefs)
+    cp = getattr(basis, "coefs_p", None)
+    cp = _as_f64(cp) if cp is not None else None
+    keep += [at, l, npr, ex, co, cp]
+    return Basis_c(int(l.shape[0]), at.ctypes.data_as(_i32p), l.ctypes.data_as(_i32p), npr.ctypes.data_as(_i32p),
+                   ex.ctypes.data_as(_f64p), co.ctypes.data_as(_f64p),
+                   cp.ctypes.data_as(_f64p) if cp is not None else None)
 
 
 class Thresholds_c(ctypes.Structure):
@@ -236,11 +251,9 @@ class System:
                  fp32_cutoff: float = 0.0, prim_tau: float = 0.0):
         self.ctx = ctx
         Z, xyz = _as_i32(geom.Z), _as_f64(geom.xyz)
-        at, l, npr = _as_i32(basis.atom), _as_i32(basis.l), _as_i32(basis.nprim)
-        ex, co = _as_f64(basis.exps), _as_f64(basis.coefs)
+        keep = []
         g = Geometry_c(int(Z.shape[0]), Z.ctypes.data_as(_i32p), xyz.ctypes.data_as(_f64p))
-        b = Basis_c(int(l.shape[0]), at.ctypes.data_as(_i32p), l.ctypes.data_as(_i32p), npr.ctypes.data_as(_i32p),
-                    ex.ctypes.data_as(_f64p), co.ctypes.data_as(_f64p))
+        b = _basis_c(basis, keep)
         th = Thresholds_c(float(schwarz_tau), float(fp32_cutoff), float(prim_tau))
         self._h = ctypes.c_void_p()
         _check(load_library().hf_system_create(ctx._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(th),
@@ -339,12 +352,10 @@ class Batch:
         G = (Geometry_c * n)()
         Bs = (Basis_c * n)()
         for m, (g, b) in enumerate(zip(geoms, bases)):
-            arrs = [_as_i32(g.Z), _as_f64(g.xyz), _as_i32(b.atom), _as_i32(b.l), _as_i32(b.nprim), _as_f64(b.exps),
-                    _as_f64(b.coefs)]
+            arrs = [_as_i32(g.Z), _as_f64(g.xyz)]
             keep.append(arrs)
             G[m] = Geometry_c(int(arrs[0].shape[0]), arrs[0].ctypes.data_as(_i32p), arrs[1].ctypes.data_as(_f64p))
-            Bs[m] = Basis_c(int(arrs[3].shape[0]), arrs[2].ctypes.data_as(_i32p), arrs[3].ctypes.data_as(_i32p),
-                            arrs[4].ctypes.data_as(_i32p), arrs[5].ctypes.data_as(_f64p), arrs[6].ctypes.data_as(_f64p))
+            Bs[m] = _basis_c(b, keep)
         th = Thresholds_c(float(schwarz_tau), 0.0, float(prim_tau))
         self._h = ctypes.c_void_p()
         _check(load_library().hf_batch_create(ctx._h, n, G, Bs, ctypes.byref(th), ctypes.byref(self._h)),

@@ -85,7 +85,8 @@ class Basis:
     l: np.ndarray        # int32 [n_shells] angular momentum 0..2
     nprim: np.ndarray    # int32 [n_shells]
     exps: np.ndarray     # float64 [sum nprim] primitive exponents
-    coefs: np.ndarray    # float64 [sum nprim] coefficients on normalised primitives
+    coefs: np.ndarray    # float64 [sum nprim] coefficients on normalised primitives (s part of sp shells)
+    coefs_p: np.ndarray | None = None  # float64 [sum nprim] p coefficients of sp shells (l = -1), else unused
 
     @property
     def n_shells(self) -> int:
@@ -198,6 +199,37 @@ def synthetic_basis(geom: Geometry) -> Basis:
     return Basis(atom=np.array(atom, dtype=np.int32), l=np.array(l, dtype=np.int32),
                  nprim=np.array(nprim, dtype=np.int32), exps=np.array(exps, dtype=np.float64),
                  coefs=np.array(coefs, dtype=np.float64))
+
+
+# Split-valence synthetic basis with sp (L) shells (the shape of 6-31G(d): core s, two sp valence shells,
+# polarisation d on O; two s on H): per shell (l, base exponent, s coefficients, p coefficients), the
+# primitive exponents being base * PRIM_SCALE[:n] for n coefficients.  l = -1 is an sp shell.
+SP_SHELLS_BY_Z = {
+    8: [(0, 20.0, (0.4, 0.4, 0.2), None),
+        (-1, 1.2, (-0.1, 0.5, 0.6), (0.3, 0.5, 0.3)),
+        (-1, 0.25, (1.0,), (1.0,)),
+        (2, 0.8, (1.0,), None)],
+    1: [(0, 1.5, (0.4, 0.4, 0.2), None),
+        (0, 0.15, (1.0,), None)],
+}
+
+
+def synthetic_sp_basis(geom: Geometry) -> Basis:
+    """The split-valence synthetic basis: 15 functions on O (s, sp, sp, d), 2 on H (s, s)."""
+    atom, l, nprim, exps, coefs, coefs_p = [], [], [], [], [], []
+    for a, z in enumerate(geom.Z.tolist()):
+        if z not in SP_SHELLS_BY_Z:
+            raise ValueError(f"no basis for Z={z}")
+        for (lq, base, cs, cp) in SP_SHELLS_BY_Z[z]:
+            atom.append(a)
+            l.append(lq)
+            nprim.append(len(cs))
+            exps.extend(base * s for s in PRIM_SCALE[:len(cs)])
+            coefs.extend(cs)
+            coefs_p.extend(cp if cp is not None else (0.0,) * len(cs))
+    return Basis(atom=np.array(atom, dtype=np.int32), l=np.array(l, dtype=np.int32),
+                 nprim=np.array(nprim, dtype=np.int32), exps=np.array(exps, dtype=np.float64),
+                 coefs=np.array(coefs, dtype=np.float64), coefs_p=np.array(coefs_p, dtype=np.float64))
 
 
 def random_orbitals(n_bf: int, n_occ: int, config_id: int, index: int = 0) -> np.ndarray:

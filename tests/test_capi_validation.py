@@ -55,6 +55,7 @@ def test_null_context():
     ("nan_coordinate", hf.HF_E_INVALID),
     ("atom_out_of_range", hf.HF_E_INVALID),
     ("negative_l", hf.HF_E_INVALID),
+    ("sp_without_p_coefficients", hf.HF_E_INVALID),
     ("f_shell", hf.HF_E_UNSUPPORTED),
     ("no_primitives", hf.HF_E_INVALID),
     ("nine_primitives", hf.HF_E_UNSUPPORTED),
@@ -79,7 +80,9 @@ def test_malformed_input_is_rejected(case, code):
     elif case == "atom_out_of_range":
         atom[4] = 3
     elif case == "negative_l":
-        l[0] = -1
+        l[0] = -2
+    elif case == "sp_without_p_coefficients":
+        l[1] = hf.HF_SP_SHELL  # coefs_p is NULL in _create
     elif case == "f_shell":
         l[5] = 3
     elif case == "no_primitives":

@@ -107,8 +107,12 @@ def test_batch_screened_members_vs_oracle(ctx, oracle_mod):
         _, H = mol.core_hamiltonian()
         Fo = oracle_mod.fock_from_jk(H, J, K)
         got = F[int(batch.offsets[m]):int(batch.offsets[m + 1])].cpu().numpy().reshape(n, n)
-        assert np.abs(got - Fo).max() <= 1e-10
-        assert abs(E[m] - oracle_mod.electronic_energy(Pm, H, Fo)) <= 1e-9
+        dF = np.abs(got - Fo).max()
+        assert dF <= 1e-10
+        # E = 1/2 sum P (H + F): an F error of dF moves it by at most 1/2 sum |P| dF, plus the rounding of a
+        # sum of n^2 terms of this (large, random-density) energy
+        Eo = oracle_mod.electronic_energy(Pm, H, Fo)
+        assert abs(E[m] - Eo) <= 0.5 * np.abs(Pm).sum() * dF + 1e-14 * n * abs(Eo)
 
 
 def test_batch_rejects_bad_density(ctx):

@@ -298,3 +298,37 @@ def test_private_fock_copies(ctx, oracle_mod, copies):
     assert np.abs(again["F"] - shared["F"]).max() <= 1e-12
     with pytest.raises(hf.HFError):
         s.set_fock_copies(0)
+
+
+def test_sp_shell_basis_four_waters_unscreened(ctx, oracle_mod):
+    """A split-valence basis with sp (L) shells (s, sp, sp, d on O; s, s on H; 76 functions at 4 waters):
+    the library takes the sp shells as given and matches the oracle's unscreened J, K, F and one-electron
+    matrices within the FP64 tolerance."""
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(4, I.CONFIG_SINGLE_BUILD)
+    basis = I.synthetic_sp_basis(geom)
+    assert (basis.l == -1).sum() == 8
+    mol = oracle_mod.Molecule(geom, basis)
+    S, H = mol.core_hamiltonian()
+    P = _density(oracle_mod, mol, 20, I.CONFIG_SINGLE_BUILD, 0)
+    J, K = mol.jk_literal(P)
+    F = oracle_mod.fock_from_jk(H, J, K)
+    s = hf.System(ctx, geom, basis)
+    assert s.n_bf == mol.n_bf == 76
+    Sg, Hg = s.one_electron()
+    assert np.abs(Sg - S).max() < 1e-13 and np.abs(Hg - H).max() < 1e-11
+    out = s.fock_build(P, want_J=True, want_K=True)
+    assert np.abs(out["J"] - J).max() <= 1e-10
+    assert np.abs(out["K"] - K).max() <= 1e-10
+    assert np.abs(out["F"] - F).max() <= 1e-10
+    assert abs(out["E_elec"] - oracle_mod.electronic_energy(P, H, F)) <= 1e-9
+
+
+def test_sp_shell_basis_scf_vs_oracle(ctx, oracle_mod):
+    from paper_1708_00033_gb300 import hf
+    geom = I.water_cluster(2, 2, 8)
+    basis = I.synthetic_sp_basis(geom)
+    r = hf.scf(hf.System(ctx, geom, basis, schwarz_tau=1e-12), e_tol=1e-11, d_tol=1e-8)
+    ref = oracle_mod.scf(oracle_mod.Molecule(geom, basis), e_tol=1e-11, d_tol=1e-8)
+    assert r["converged"] and ref.converged
+    assert abs(r["energy"] - ref.energy) < 1e-9

@@ -181,9 +181,10 @@ def test_training_and_learned_scf(ctx):
 
 def test_trained_network_gain():
     """The shipped network (trained by train_guess.py on plain-SCF densities of 2-8 water clusters) against
-    the method without it, on held-out clusters (seeds (6, m), never trained on): the SCF from the learned
-    density needs fewer iterations than the SCF from the core-Hamiltonian guess, on every cluster and by at
-    least a third on average, and converges to the same energy within 1e-8 Eh."""
+    the method without it, on held-out clusters of 10-16 waters (seeds (6, m), never trained on, larger
+    than any training cluster): the SCF from the learned density needs fewer iterations than the SCF from
+    the core-Hamiltonian guess on every cluster, at most 0.7 times as many on average, and converges to the
+    same energy within 1e-8 Eh."""
     import os
     from paper_1708_00033_gb300 import guess, hf
     assert os.path.exists(guess.WEIGHTS_PATH), "trained weights are missing"
@@ -191,7 +192,7 @@ def test_trained_network_gain():
     ctx = hf.Context(0)
     model = hf.Model(ctx, w)
     core_it, learned_it = [], []
-    for m, nw in enumerate((4, 6, 8, 10)):
+    for m, nw in enumerate((10, 12, 14, 16)):
         geom = I.water_cluster(nw, I.CONFIG_GUESS_EVAL, 100 + m)
         basis = I.synthetic_basis(geom)
         s = hf.System(ctx, geom, basis, schwarz_tau=1e-10, prim_tau=I.BENCH_PRIM_TAU)
@@ -204,4 +205,4 @@ def test_trained_network_gain():
         assert learned["iterations"] < core["iterations"], (nw, learned["iterations"], core["iterations"])
         core_it.append(core["iterations"])
         learned_it.append(learned["iterations"])
-    assert np.mean(learned_it) <= (2.0 / 3.0) * np.mean(core_it), (core_it, learned_it)
+    assert np.mean(learned_it) <= 0.7 * np.mean(core_it), (core_it, learned_it)

@@ -379,3 +379,39 @@ def test_screened_elements_and_blocks_vs_unique(oracle_mod):
     Je, Ke = m.jk_elements(P, pairs, tau=tau)
     for t, (mu, nu) in enumerate(pairs):
         assert abs(Je[t] - Ju[mu, nu]) < 1e-12 and abs(Ke[t] - Ku[mu, nu]) < 1e-12
+
+
+def test_sp_shell_is_an_s_and_a_p_shell(oracle_mod):
+    """An sp shell is by definition an s and a p shell with the same exponents and their own coefficients:
+    a basis written with sp shells gives the same S, H and SCF energy as the same shells written out
+    separately by hand (s coefficients in the s shell, p coefficients in the p shell)."""
+    g = I.water_cluster(1, 2, 1)
+    sp = I.synthetic_sp_basis(g)
+    atom, l, nprim, exps, coefs = [], [], [], [], []
+    o = 0
+    for s_ in range(sp.n_shells):
+        n = int(sp.nprim[s_])
+        parts = [(0, sp.coefs), (1, sp.coefs_p)] if sp.l[s_] == -1 else [(int(sp.l[s_]), sp.coefs)]
+        for lq, c in parts:
+            atom.append(int(sp.atom[s_]))
+            l.append(lq)
+            nprim.append(n)
+            exps += list(sp.exps[o:o + n])
+            coefs += list(c[o:o + n])
+        o += n
+    sep = I.Basis(atom=np.array(atom, dtype=np.int32), l=np.array(l, dtype=np.int32),
+                  nprim=np.array(nprim, dtype=np.int32), exps=np.array(exps), coefs=np.array(coefs))
+    m_sp, m_sep = oracle_mod.Molecule(g, sp), oracle_mod.Molecule(g, sep)
+    assert m_sp.n_bf == m_sep.n_bf == 15 + 2 + 2
+    S1, H1 = m_sp.core_hamiltonian()
+    S2, H2 = m_sep.core_hamiltonian()
+    assert np.abs(S1 - S2).max() == 0.0 and np.abs(H1 - H2).max() == 0.0
+    assert np.allclose(np.diag(S1), 1.0, atol=1e-14)
+    # the p functions of an sp shell use the p coefficients: a basis whose sp shells take their s
+    # coefficients for p too is a different basis
+    same = I.Basis(atom=sp.atom, l=sp.l, nprim=sp.nprim, exps=sp.exps, coefs=sp.coefs, coefs_p=sp.coefs.copy())
+    S3, _ = oracle_mod.Molecule(g, same).core_hamiltonian()
+    assert np.abs(S3 - S1).max() > 1e-3
+    e1 = oracle_mod.scf(m_sp, e_tol=1e-11, d_tol=1e-8)
+    e2 = oracle_mod.scf(m_sep, e_tol=1e-11, d_tol=1e-8)
+    assert e1.converged and abs(e1.energy - e2.energy) < 1e-12
