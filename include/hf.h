@@ -55,6 +55,11 @@ extern "C" {
 #define HF_FP64_ONLY 8  /* hf_fock_build: evaluate the FP32 part of a mixed system in FP64 too */
 #define HF_DENSITY_SCREEN 16 /* hf_fock_build_partial: also skip quartets whose Schwarz bound times the
                                 largest |P| of the six density blocks they touch (x4) is below schwarz_tau */
+#define HF_RYS 32            /* hf_fock_build, hf_fock_build_partial: evaluate the FP64 quartets of the classes
+                                of total angular momentum L >= 6 ((dp|dp), (dd|pp), (dd|ds), (dd|dp),
+                                (dd|dd)) by Rys quadrature (L/2 + 1 nodes of the Boys weight) instead of the
+                                Obara-Saika vertical recurrence; the contraction, horizontal recurrence and
+                                digestion are shared, so results agree to rounding */
 
 typedef struct hf_ctx hf_ctx;       /* one device + one stream + constant tables */
 typedef struct hf_system hf_system; /* one molecule: basis, pairs, screening plan, 1e matrices */
@@ -195,7 +200,7 @@ int hf_one_electron(hf_system* sys, double* S, double* H, int flags);
  *   E_elec host scalar output 1/2 sum P (H + F) (may be NULL).
  *   stats  host output (may be NULL); HF_TIMING adds device times.
  * flags: HF_PTR_DEVICE (P, F, J, K are device pointers), HF_TIMING,
- * HF_FP64_ONLY.  The density check runs on the device: the host waits once,
+ * HF_FP64_ONLY, HF_RYS.  The density check runs on the device: the host waits once,
  * after the whole build, and a rejected density leaves every output
  * untouched.
  * Errors: HF_E_INVALID (NULL sys/P, P not finite or not symmetric),
@@ -243,7 +248,7 @@ int hf_system_set_fock_copies(hf_system* sys, int32_t copies);
  * 1/2 sum_s K_s: the counterpart of the paper's per-rank partial Fock matrix
  * and ddi_gsumf (Algorithms 1-3), with the sum left to the caller (for
  * example one allreduce of J and K).  J, K: [N*N] outputs (required).
- * flags: HF_PTR_DEVICE, HF_FP64_ONLY, HF_DENSITY_SCREEN (density-weighted
+ * flags: HF_PTR_DEVICE, HF_FP64_ONLY, HF_RYS, HF_DENSITY_SCREEN (density-weighted
  * Schwarz screening: the J and K of a density difference, as in incremental
  * SCF builds).  Errors: HF_E_INVALID (bad shard, NULL pointer, P not finite
  * or not symmetric), HF_E_CUDA. */
@@ -412,7 +417,7 @@ int hf_batch_tune(hf_batch* batch, const char* cache_path, int64_t sample_quarte
 
 typedef struct hf_model hf_model;
 
-/* Number of floats in the weight vector (158,277). */
+/* Number of floats in the weight vector (153,669). */
 int64_t hf_model_num_params(void);
 
 /* Create a model from host weights (hf_model_num_params floats). */

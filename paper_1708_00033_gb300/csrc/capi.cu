@@ -155,7 +155,10 @@ int hf_create(hf_ctx** out, int device, void* cuda_stream)
         // Reserve per-thread local memory for the largest ERI kernel once, so that launches of the
         // spilling high-angular-momentum kernels do not grow and shrink the reservation each time.
         size_t need = 0;
-        for (int ci = 0; ci < kNumClasses; ci++) need = std::max(need, kEriClasses[ci].local_bytes());
+        for (int ci = 0; ci < kNumClasses; ci++) {
+            need = std::max(need, kEriClasses[ci].local_bytes());
+            if (kEriClasses[ci].local_bytes_rys) need = std::max(need, kEriClasses[ci].local_bytes_rys());
+        }
         size_t cur = 0;
         if (cudaDeviceGetLimit(&cur, cudaLimitStackSize) == cudaSuccess && need > cur)
             if (cudaDeviceSetLimit(cudaLimitStackSize, need) != cudaSuccess)
@@ -705,6 +708,13 @@ int hf_system_set_fock_copies(hf_system* S, int32_t copies)
 
 }  // extern "C"
 
+// Whether a launch of class ci runs the Rys-quadrature kernel: asked for (HF_RYS), an FP64 launch, a class
+// that has one, and the ket tables in use.
+static bool uses_rys(int ci, int flags, int use_f32, const EriArgs& a)
+{
+    return (flags & HF_RYS) && !use_f32 && kEriClasses[ci].launch_rys && a.kt;
+}
+
 // The per-class ERI launches shared by hf_fock_build, hf_fock_build_partial and hf_fock_build_noalloc.
 int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int flags, cudaEvent_t* ev,
                            unsigned long long* prim_count)
@@ -755,7 +765,10 @@ int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int
                 const int lanes = (!use_f32 && q1 - q0 < (long long)ctx->num_sms * 256) ? kEriClasses[ci].lanes : 1;
                 const long long blocks = ((q1 - q0) * lanes + kEriThreads - 1) / kEriThreads;
                 const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
-                kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st, lanes);
+                if (uses_rys(ci, flags, use_f32, a))
+                    kEriClasses[ci].launch_rys(a, 0, grid, kEriThreads, st, lanes);
+                else
+                    kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st, lanes);
                 HF_CUDA(cudaGetLastError());
             }
             if (ev) HF_CUDA(cudaEventRecord(ev[4 * ci + 2 * prec + 1], st));
@@ -838,8 +851,11 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
             stats->prim_quartets_fp64 += (int64_t)pc[2 * ci];
             stats->prim_quartets_fp32 += (int64_t)pc[2 * ci + 1];
             const double pf = kEriClasses[ci].prim_flops, cf = kEriClasses[ci].cont_flops;
-            stats->class_flops_fp64[ci] = pf * (double)pc[2 * ci] + cf * (double)pl.n64;
-            stats->class_flops_fp32[ci] = pf * (double)pc[2 * ci + 1] + cf * (double)pl.n32;
+            const bool rys = (flags & HF_RYS) && kEriClasses[ci].launch_rys && X.ket_soa;
+            const double pf64 = rys ? kEriClasses[ci].prim_flops_rys : pf;
+            const double pf32 = (rys && (flags & HF_FP64_ONLY)) ? pf64 : pf;  // FP32 launches stay Obara-Saika
+            stats->class_flops_fp64[ci] = pf64 * (double)pc[2 * ci] + cf * (double)pl.n64;
+            stats->class_flops_fp32[ci] = pf32 * (double)pc[2 * ci + 1] + cf * (double)pl.n32;
             stats->flops_fp64 += stats->class_flops_fp64[ci];
             stats->flops_fp32 += stats->class_flops_fp32[ci];
             stats->kernels_launched += (pl.n64 > 0) + (pl.n32 > 0);

@@ -237,9 +237,7 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
 
 // Kernels and host launchers of one class.  The digestion weight of a unique
 // shell quartet is f = 1/((1+d_AB)(1+d_CD)(1+d_AB,CD)).
-#define ERI_CLASS_KERNELS(NAME, X, Y, GL)                                                                    \
-    template <typename real, int GK, bool SOA>                                                               \
-    __global__ void __launch_bounds__(kEriThreads) k_eri_##NAME(const EriArgs a)                            \
+#define ERI_KERNEL_BODY(QFN)                                                                                 \
     {                                                                                                        \
         if (a.bad && *a.bad) return; /* rejected density: grid-uniform exit, outputs untouched */            \
         const PrimPair<real>* prims = (const PrimPair<real>*)(sizeof(real) == 8 ? a.prims64 : a.prims32);   \
@@ -300,11 +298,11 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
             }                                                                                                \
             if constexpr (SOA) {                                                                             \
                 const KetSoa<real> kv{(const real*)a.kt + k, a.ktB + k, a.kstride};                          \
-                nprimq += quartet_##NAME<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
+                nprimq += QFN<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
                                                    live);                                                    \
             } else {                                                                                         \
                 const KetAos<real> kv{kst ? kst : prims + hk.prim0};                                         \
-                nprimq += quartet_##NAME<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
+                nprimq += QFN<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
                                                    live);                                                    \
             }                                                                                                \
         }                                                                                                    \
@@ -312,7 +310,12 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
             const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \
             if ((threadIdx.x & 31) == 0 && w) atomicAdd(a.prim_count, w);                                    \
         }                                                                                                    \
-    }                                                                                                        \
+    }
+
+#define ERI_CLASS_KERNELS(NAME, X, Y, GL)                                                                    \
+    template <typename real, int GK, bool SOA>                                                               \
+    __global__ void __launch_bounds__(kEriThreads) k_eri_##NAME(const EriArgs a)                            \
+    ERI_KERNEL_BODY(quartet_##NAME)                                                                          \
     void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s, int lanes)   \
     {                                                                                                        \
         const bool soa = a.kt != nullptr;                                                                    \
@@ -343,6 +346,30 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
         for (const void* fn : fns)                                                                           \
             if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.localSizeBytes > m) m = fa.localSizeBytes; \
         if (cudaFuncGetAttributes(&fa, k_eri_batch_##NAME) == cudaSuccess && fa.localSizeBytes > m)          \
+            m = fa.localSizeBytes;                                                                           \
+        cudaGetLastError();                                                                                  \
+        return m;                                                                                            \
+    }
+
+// Rys-quadrature variant of a class: the same kernel body around quartet_rys_NAME, FP64 and the ket
+// tables only (launch_eri_rys_NAME is given FP64 launches with a.kt set).
+#define ERI_RYS_KERNELS(NAME, GL)                                                                            \
+    template <typename real, int GK, bool SOA>                                                               \
+    __global__ void __launch_bounds__(kEriThreads) k_eri_rys_##NAME(const EriArgs a)                        \
+    ERI_KERNEL_BODY(quartet_rys_##NAME)                                                                      \
+    void launch_eri_rys_##NAME(const EriArgs& a, int, int grid, int block, cudaStream_t s, int lanes)       \
+    {                                                                                                        \
+        if (lanes > 1)                                                                                       \
+            k_eri_rys_##NAME<double, (GL), true><<<grid, block, 0, s>>>(a);                                  \
+        else                                                                                                 \
+            k_eri_rys_##NAME<double, 1, true><<<grid, block, 0, s>>>(a);                                     \
+    }                                                                                                        \
+    size_t local_bytes_rys_##NAME()                                                                          \
+    {                                                                                                        \
+        cudaFuncAttributes fa;                                                                               \
+        size_t m = 0;                                                                                        \
+        if (cudaFuncGetAttributes(&fa, k_eri_rys_##NAME<double, 1, true>) == cudaSuccess) m = fa.localSizeBytes; \
+        if (cudaFuncGetAttributes(&fa, k_eri_rys_##NAME<double, (GL), true>) == cudaSuccess && fa.localSizeBytes > m) \
             m = fa.localSizeBytes;                                                                           \
         cudaGetLastError();                                                                                  \
         return m;                                                                                            \

@@ -181,6 +181,110 @@ def gen_vrr(la, lb, lc, ld, cnt):
     return lines, acc, used, targets
 
 
+RYS_MIN_L = 6  # classes evaluated by Rys quadrature when asked for (HF_RYS)
+
+
+def gen_rys_prim(la, lb, lc, ld, cnt):
+    """Rys quadrature replacement of the vertical step for one primitive quartet: with the n = L/2 + 1
+    nodes u_r = t_r^2 and weights w_r of the Boys weight at T (rys.cuh), and per node the 2D integrals
+    G_d(a, c), d = x, y, z, a <= la + lb, c <= lc + ld, from
+        G(0, 0) = 1 (x, y), pref w_r (z),
+        G(a+1, 0) = C00 G(a, 0) + a B10 G(a-1, 0),
+        G(a, c+1) = C00' G(a, c) + c B01 G(a, c-1) + a B00 G(a-1, c),
+    with B00 = u / (2(p+q)), B10 = (1 - rho u / p) / (2p), B01 = (1 - rho u / q) / (2q),
+    C00 = PA - (rho / p) u PQ, C00' = QC + (rho / q) u PQ (the Obara-Saika terms of the vertical
+    recurrence with the m-th Boys value replaced by the m-th power of u), the targets are
+    [e0|f0] += G_x(e_x, f_x) G_y(e_y, f_y) G_z(e_z, f_z), summed over the nodes.
+    Returns (setup lines, per-primitive body lines, targets, setup flop count)."""
+    L = la + lb + lc + ld
+    n = L // 2 + 1
+    targets = [(e, f, 0) for le in range(la, la + lb + 1) for e in CART[le]
+               for lf in range(lc, lc + ld + 1) for f in CART[lf]]
+    need = [set(), set(), set()]
+    for e, f, _ in targets:
+        for d in range(3):
+            need[d].add((e[d], f[d]))
+    # dependency closure in recurrence order
+    for d in range(3):
+        stack = list(need[d])
+        while stack:
+            a, c = stack.pop()
+            deps = []
+            if c > 0:
+                deps = [(a, c - 1)] + ([(a, c - 2)] if c >= 2 else []) + ([(a - 1, c - 1)] if a >= 1 else [])
+            elif a > 0:
+                deps = [(a - 1, 0)] + ([(a - 2, 0)] if a >= 2 else [])
+            for x in deps:
+                if x not in need[d]:
+                    need[d].add(x)
+                    stack.append(x)
+    setup = [
+        "const real s = bp.p + kp.p;",
+        "const real rs = rsq(s);",
+        "const real inv = rs * rs;",
+        "const real PQx = bp.Px - kp.Px, PQy = bp.Py - kp.Py, PQz = bp.Pz - kp.Pz;",
+        "const real rho = bp.p * kp.p * inv;",
+        "const real T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);",
+        "const real pref = bK * kp.K * rs;",
+        "const real rho_p = kp.p * inv, rho_q = bp.p * inv, o2pq_1 = real(0.5) * inv, ko2p = kp.oo2p;",
+        "const real QCx = kp.PAx, QCy = kp.PAy, QCz = kp.PAz;",
+        f"real ru[{n}], rw[{n}];",
+        f"rys_rule<{n}>(T, ru, rw);",
+    ]
+    cset = 1 + 8 + 1 + 3 + 2 + 6 + 2 + 3 + 2 * n * 2 * 11 + 4
+    body = [f"#pragma unroll 1", f"for (int r = 0; r < {n}; r++) {{",
+            "    const real u = ru[r];",
+            "    const real B00 = o2pq_1 * u;",
+            "    const real B10 = bo2p - bo2p * rho_p * u;",
+            "    const real B01 = ko2p - ko2p * rho_q * u;",
+            "    const real up = rho_p * u, uq = rho_q * u;"]
+    fl = 1 + 3 + 3 + 2
+    for d, ax in enumerate(AX):
+        body.append(f"    const real C{ax} = PA{ax} - up * PQ{ax}, D{ax} = QC{ax} + uq * PQ{ax};")
+        fl += 4
+    body.append("    const real gz_0_0 = pref * rw[r];")
+    fl += 1
+    for d, ax in enumerate(AX):
+        g = f"g{ax}"
+        nd = need[d]
+        amax = max(a for a, c in nd)
+        cmax = max(c for a, c in nd)
+        for c in range(cmax + 1):
+            for a in range(amax + 1):
+                if (a, c) not in nd or (a, c) == (0, 0):
+                    continue
+                if c == 0:
+                    expr = f"C{ax} * {g}_{a - 1}_0"
+                    fl += 1
+                    if a >= 2:
+                        expr += f" + real({a - 1}) * B10 * {g}_{a - 2}_0"
+                        fl += 3
+                else:
+                    expr = f"D{ax} * {g}_{a}_{c - 1}"
+                    fl += 1
+                    if c >= 2:
+                        expr += f" + real({c - 1}) * B01 * {g}_{a}_{c - 2}"
+                        fl += 3
+                    if a >= 1:
+                        expr += f" + real({a}) * B00 * {g}_{a - 1}_{c - 1}"
+                        fl += 3
+                body.append(f"    const real {g}_{a}_{c} = {expr};")
+    for ax in "xy":
+        body.insert(len(body) - sum(1 for _ in []), "")
+    # G_x(0,0) = G_y(0,0) = 1: substitute the literal
+    body = [l.replace("gx_0_0", "real(1)").replace("gy_0_0", "real(1)") for l in body if l != ""]
+    for e, f, _ in targets:
+        gx = f"gx_{e[0]}_{f[0]}" if (e[0], f[0]) != (0, 0) else None
+        gy = f"gy_{e[1]}_{f[1]}" if (e[1], f[1]) != (0, 0) else None
+        gz = f"gz_{e[2]}_{f[2]}"
+        prod = " * ".join(x for x in (gx, gy, gz) if x)
+        body.append(f"    acc{tstr(e)}_{tstr(f)} += {prod};")
+        fl += 1 + (1 if gx else 0) + (1 if gy else 0)
+    body.append("}")
+    cnt.prim += fl * n
+    return setup, body, targets, cset
+
+
 def gen_setup(L, used, cnt):
     """Per-primitive-quartet quantities; returns lines (flop counts approximate the emitted ops)."""
     lines = [
@@ -358,18 +462,29 @@ def class_name(X, Y):
     return f"{la}{lb}{lc}{ld}"
 
 
-def gen_class(X, Y):
+def gen_class(X, Y, method="os"):
+    """Source of one class's quartet function and kernels: method "os" (Obara-Saika vertical step, Boys
+    table) or "rys" (Rys quadrature vertical step); both share the contraction, HRR and digestion."""
     la, lb = PAIR_CLASSES[X]
     lc, ld = PAIR_CLASSES[Y]
     L = la + lb + lc + ld
     name = class_name(X, Y)
     cnt = Counter()
-    vrr, acc, used, targets = gen_vrr(la, lb, lc, ld, cnt)
-    setup, cset = gen_setup(L, used, cnt)
+    if method == "os":
+        vrr, acc, used, targets = gen_vrr(la, lb, lc, ld, cnt)
+        setup, cset = gen_setup(L, used, cnt)
+        extra = boys_flops(L)
+        qname = f"quartet_{name}"
+    else:
+        setup, vrr, targets, cset = gen_rys_prim(la, lb, lc, ld, cnt)
+        acc = []
+        used = {"PAx", "PAy", "PAz"}
+        extra = 0
+        qname = f"quartet_rys_{name}"
     hrr, xname = gen_hrr(la, lb, lc, ld, cnt)
     cont_hrr = cnt.cont
     dig = gen_digest(la, lb, lc, ld, xname, cnt)
-    prim_flops = cnt.prim + cset + boys_flops(L)
+    prim_flops = cnt.prim + cset + extra
     acc_decl = [f"real acc{tstr(e)}_{tstr(f)} = real(0);" for (e, f, m) in targets]
     need_ab = any("AB" in l for l in hrr)
     need_cd = any("CD" in l for l in hrr)
@@ -377,14 +492,14 @@ def gen_class(X, Y):
     out = []
     out.append(f"// ({PAIR_NAMES[X]}|{PAIR_NAMES[Y]}) class: l = {la}{lb}{lc}{ld}, "
                f"{len(targets)} [e0|f0] targets, {prim_flops} flops per primitive quartet, "
-               f"{cnt.cont} per contracted quartet.")
+               f"{cnt.cont} per contracted quartet" + (", Rys quadrature." if method == "rys" else "."))
     G = LANES_BY_L[L]
     out.append(f"// Lanes per quartet in the ERI kernels: {G}.  The G lanes of a group share one shell quartet's")
     out.append(f"// primitive staircase round-robin and sum their accumulators with butterfly shuffles; lane 0")
     out.append(f"// then runs the horizontal recurrence and the digestion.  Called warp-uniformly; a lane with")
     out.append(f"// valid == false takes part in the shuffles only.")
     out.append(f"template <typename real, int G, typename KV>")
-    out.append(f"__device__ __forceinline__ int quartet_{name}(const PairHdr& hb, const PairHdr& hk, const KV& kv,"
+    out.append(f"__device__ __forceinline__ int {qname}(const PairHdr& hb, const PairHdr& hk, const KV& kv,"
                f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
     out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
     out.append(f"    float ptau, int lane, bool valid)")
@@ -447,31 +562,33 @@ def gen_class(X, Y):
     out.append("        }")
     out.append("    }")
     out.append("    if (!valid || lane != 0) return nq;")
+    tail = []
     if need_ab:
-        out.append("    const real ABx = (real)hb.ABx, ABy = (real)hb.ABy, ABz = (real)hb.ABz;")
+        tail.append("const real ABx = (real)hb.ABx, ABy = (real)hb.ABy, ABz = (real)hb.ABz;")
     if need_cd:
-        out.append("    const real CDx = (real)hk.ABx, CDy = (real)hk.ABy, CDz = (real)hk.ABz;")
-    for l in hrr:
-        out.append("    " + l)
-    out.append("    if (qout) {")
+        tail.append("const real CDx = (real)hk.ABx, CDy = (real)hk.ABy, CDz = (real)hk.ABz;")
+    tail += hrr
+    tail.append("if (qout) {")
     if X == Y:
-        for l in gen_schwarz(la, lb, xname):
-            out.append("        " + l)
-        out.append("        *qout = qmax;")
-    out.append("        return nq;")
-    out.append("    }")
-    out.append("    if (total == 0) return nq;  // every primitive quartet screened: nothing to digest")
-    out.append("    const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
-    out.append("    const real fj = (real)(4.0 * fscale), fk = (real)(2.0 * fscale);")
-    for l in dig:
-        out.append("    " + l)
+        tail += ["    " + l for l in gen_schwarz(la, lb, xname)]
+        tail.append("    *qout = qmax;")
+    tail.append("    return;")
+    tail.append("}")
+    tail.append("if (total == 0) return;  // every primitive quartet screened: nothing to digest")
+    tail.append("const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
+    tail.append("const real fj = (real)(4.0 * fscale), fk = (real)(2.0 * fscale);")
+    tail += dig
+    out += ["    " + l.replace("return;", "return nq;") for l in tail]
     out.append("    return nq;")
     out.append("}")
     out.append("")
-    out.append(f"ERI_BATCH_KERNEL({name}, {G})")
-    out.append(f"ERI_CLASS_KERNELS({name}, {X}, {Y}, {G})")
-    if X == Y:
-        out.append(f"SCHWARZ_KERNEL({name})")
+    if method == "rys":
+        out.append(f"ERI_RYS_KERNELS({name}, {G})")
+    else:
+        out.append(f"ERI_BATCH_KERNEL({name}, {G})")
+        out.append(f"ERI_CLASS_KERNELS({name}, {X}, {Y}, {G})")
+        if X == Y:
+            out.append(f"SCHWARZ_KERNEL({name})")
     info = dict(name=name, X=X, Y=Y, l=[la, lb, lc, ld], L=L, G=G, prim_flops=prim_flops, cont_flops=cnt.cont,
                 hrr_flops=cont_hrr, targets=len(targets), vrr_nodes=len(vrr))
     return "\n".join(out) + "\n", info
@@ -496,6 +613,16 @@ def main(outdir):
         if not os.path.exists(path) or open(path).read() != text:
             with open(path, "w") as fh:
                 fh.write(text)
+        info["rys"] = info["L"] >= RYS_MIN_L
+        info["prim_flops_rys"] = 0
+        if info["rys"]:
+            rsrc, rinfo = gen_class(X, Y, "rys")
+            info["prim_flops_rys"] = rinfo["prim_flops"]
+            path = os.path.join(outdir, f"eri_rys_{info['name']}.cu")
+            text = HEADER.replace('#include "eri_common.cuh"', '#include "eri_common.cuh"\n#include "rys.cuh"') + rsrc + FOOTER
+            if not os.path.exists(path) or open(path).read() != text:
+                with open(path, "w") as fh:
+                    fh.write(text)
     # dispatch table
     lines = ['// Generated by gen_eri.py: do not edit.', '#include "eri_common.cuh"', "", "namespace hf {"]
     for info in infos:
@@ -505,13 +632,18 @@ def main(outdir):
             lines.append(f"void launch_schwarz_{n}(const SchwarzArgs&, int, cudaStream_t);")
         lines.append(f"void launch_eri_batch_{n}(const BatchArgs&, int, int, cudaStream_t);")
         lines.append(f"size_t local_bytes_{n}();")
+        if info["rys"]:
+            lines.append(f"void launch_eri_rys_{n}(const EriArgs&, int, int, int, cudaStream_t, int);")
+            lines.append(f"size_t local_bytes_rys_{n}();")
     lines.append("")
     lines.append("const EriClassEntry kEriClasses[kNumClasses] = {")
     for info in infos:
         n = info["name"]
         lines.append(f"    {{{info['X']}, {info['Y']}, {info['L']}, {info['prim_flops']}, {info['cont_flops']}, "
                      f"launch_eri_{n}, {('launch_schwarz_' + n) if info['X'] == info['Y'] else 'nullptr'}, \"{n}\", "
-                     f"launch_eri_batch_{n}, local_bytes_{n}, {info['G']}}},")
+                     f"launch_eri_batch_{n}, local_bytes_{n}, {info['G']}, "
+                     + (f"launch_eri_rys_{n}, {info['prim_flops_rys']}, local_bytes_rys_{n}}}," if info["rys"]
+                        else "nullptr, 0, nullptr},"))
     lines.append("};")
     lines.append("}  // namespace hf")
     text = "\n".join(lines) + "\n"

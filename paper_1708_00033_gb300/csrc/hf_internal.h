@@ -111,6 +111,10 @@ struct EriClassEntry {
     void (*launch_batch)(const BatchArgs&, int grid, int block, cudaStream_t);
     size_t (*local_bytes)();  // largest per-thread local memory of the class's kernels
     int lanes;                // lanes that share one shell quartet in the ERI kernels
+    // Rys-quadrature variant (classes with L >= 6; nullptr otherwise): FP64 launches with ket tables
+    void (*launch_rys)(const EriArgs&, int use_f32, int grid, int block, cudaStream_t, int lanes);
+    int prim_flops_rys;       // per primitive quartet (setup + roots + 2D recurrences + accumulation)
+    size_t (*local_bytes_rys)();
 };
 extern const EriClassEntry kEriClasses[kNumClasses];
 
