@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--reference-seconds", type=float, default=150.0,
                     help="oracle time budget of --impl reference over all its steps")
     ap.add_argument("--mode", default="fock",
-                    choices=["fock", "scf", "mixed", "batch", "guess", "copies", "peaks", "shard"])
+                    choices=["fock", "scf", "mixed", "batch", "guess", "copies", "peaks", "shard", "rys"])
     ap.add_argument("--n-train", type=int, default=2000)
     ap.add_argument("--n-eval", type=int, default=32)
     ap.add_argument("--train-steps", type=int, default=4000)
@@ -604,6 +604,48 @@ def run_shard(a):
         dist.destroy_process_group()
 
 
+def run_rys(a):
+    """Rys quadrature vs Obara-Saika for the classes of total angular momentum L >= 6: per-class device time
+    of the same FP64 Fock build (best of `steps` after `warmup`), with the largest difference of F."""
+    import numpy as np
+    import torch
+    from paper_1708_00033_gb300 import hf, inputs
+    geom = inputs.water_cluster(a.waters, a.config_id, 0)
+    basis = inputs.synthetic_basis(geom)
+    ctx = hf.Context(0)
+    s = hf.System(ctx, geom, basis, schwarz_tau=a.tau, prim_tau=a.prim_tau)
+    S, _ = s.one_electron()
+    Pd = torch.from_numpy(random_density(S, inputs.n_electrons(geom) // 2, a.config_id, 0)).cuda()
+    res = {}
+    for name, rys in (("obara_saika", False), ("rys", True)):
+        F = torch.empty_like(Pd)
+        for _ in range(max(1, a.warmup)):
+            s.fock_build(Pd, F=F, rys=rys)
+        best = None
+        for _ in range(max(1, a.steps)):
+            st = s.fock_build(Pd, F=F, rys=rys, timing=True)["stats"]
+            if best is None or st["ms_eri"] < best["ms_eri"]:
+                best = st
+        res[name] = {"F": F, "stats": best}
+    L6 = [c for c in range(hf.NUM_CLASSES) if sum(int(x) for x in hf.CLASS_KERNELS[c][-4:]) >= 6]
+    rows = {}
+    for c in L6:
+        o, r = res["obara_saika"]["stats"], res["rys"]["stats"]
+        rows[hf.CLASS_NAMES[c]] = {"quartets": o["class_quartets_fp64"][c], "ms_os": o["ms_class_fp64"][c],
+                                   "ms_rys": r["ms_class_fp64"][c],
+                                   "gflops_os": o["class_flops_fp64"][c] / max(o["ms_class_fp64"][c], 1e-9) / 1e6,
+                                   "gflops_rys": r["class_flops_fp64"][c] / max(r["ms_class_fp64"][c], 1e-9) / 1e6}
+    tot_os = sum(v["ms_os"] for v in rows.values())
+    tot_rys = sum(v["ms_rys"] for v in rows.values())
+    line = {"metric": "ERI class kernel time, Rys quadrature vs Obara-Saika (L >= 6 classes)", "unit": "ms",
+            "value": tot_rys, "higher_is_better": False, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": workload_name(a)},
+            "classes": rows, "total_ms_os": tot_os, "total_ms_rys": tot_rys, "speedup_rys": tot_os / tot_rys,
+            "build_ms_os": res["obara_saika"]["stats"]["ms_total"], "build_ms_rys": res["rys"]["stats"]["ms_total"],
+            "max_abs_dF": float((res["rys"]["F"] - res["obara_saika"]["F"]).abs().max())}
+    print(json.dumps(line), flush=True)
+
+
 def _scf_run(hf, sysm, **kw):
     import torch
     torch.cuda.synchronize()
@@ -863,6 +905,8 @@ def main():
         run_peaks(a)
     elif a.mode == "shard":
         run_shard(a)
+    elif a.mode == "rys":
+        run_rys(a)
     else:
         run_ours(a)
 

@@ -565,10 +565,6 @@ int hf_system_create(hf_ctx* ctx, const hf_geometry* geom, const hf_basis* basis
     DeviceGuard g(ctx->device);
     hf_system* S = new hf_system();
     S->ctx = ctx;
-    {
-        const char* lay = getenv("HF_KET_LAYOUT");
-        S->ket_soa = !(lay && strcmp(lay, "aos") == 0);
-    }
     S->device = ctx->device;
     S->stream = ctx->stream;
     if (th) S->th = *th;
@@ -639,18 +635,6 @@ int hf_one_electron(hf_system* S, double* Sout, double* Hout, int flags)
     return HF_OK;
 }
 
-// Floats per lane of the FP32 kernels' shared-memory ket staging: one ket's primitive-pair records,
-// rounded up to an odd count; 0 (global reads) if a block's staging would exceed 48 KB, and for
-// classes of total angular momentum above 3, whose per-primitive arithmetic outweighs the loads
-// (measured at 32 waters: classes up to L = 3 gain 5-35% from staging, the higher ones 0-27% slower).
-static int fp32_stage_stride(const hf_system& X, int ci)
-{
-    if (kEriClasses[ci].L > 3) return 0;
-    int per = X.maxpp * (int)(sizeof(PrimPair<float>) / sizeof(float));
-    per |= 1;
-    return stage_bytes(per, kEriThreads) <= 48 * 1024 ? per : 0;
-}
-
 // Accumulators of one build: the system's Jt / Kt (one copy shared by every block, updated with FP64
 // atomics), or fock_copies zeroed copies of each, block b writing copy b % fock_copies, summed into
 // Jt / Kt after the ERI launches (the GPU analogue of the paper's private Fock matrices).
@@ -714,6 +698,7 @@ static bool uses_rys(int ci, int flags, int use_f32, const EriArgs& a)
 {
     return (flags & HF_RYS) && !use_f32 && kEriClasses[ci].launch_rys && a.kt;
 }
+// (the ket tables always exist for a class with significant pairs, so a.kt is set for every launch)
 
 // The per-class ERI launches shared by hf_fock_build, hf_fock_build_partial and hf_fock_build_noalloc.
 int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int flags, cudaEvent_t* ev,
@@ -748,11 +733,10 @@ int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int
                 a.q_begin = q0;
                 a.n_quartets = q1;
                 const int use_f32 = prec && !(flags & HF_FP64_ONLY);
-                a.stage_stride = use_f32 ? fp32_stage_stride(X, ci) : 0;
                 a.kt = nullptr;
                 a.ktB = nullptr;
                 a.kstride = 0;
-                if (X.ket_soa && X.ket_tab[Yc].p) {
+                if (X.ket_tab[Yc].p) {
                     const long long st_ = X.ket_stride[Yc];
                     const double* t64 = X.ket_tab[Yc].as<double>();
                     const float* t32 = (const float*)(t64 + 9 * (size_t)X.maxpp * st_);
@@ -851,7 +835,7 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
             stats->prim_quartets_fp64 += (int64_t)pc[2 * ci];
             stats->prim_quartets_fp32 += (int64_t)pc[2 * ci + 1];
             const double pf = kEriClasses[ci].prim_flops, cf = kEriClasses[ci].cont_flops;
-            const bool rys = (flags & HF_RYS) && kEriClasses[ci].launch_rys && X.ket_soa;
+            const bool rys = (flags & HF_RYS) && kEriClasses[ci].launch_rys;
             const double pf64 = rys ? kEriClasses[ci].prim_flops_rys : pf;
             const double pf32 = (rys && (flags & HF_FP64_ONLY)) ? pf64 : pf;  // FP32 launches stay Obara-Saika
             stats->class_flops_fp64[ci] = pf64 * (double)pc[2 * ci] + cf * (double)pl.n64;

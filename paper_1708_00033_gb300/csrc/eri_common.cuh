@@ -208,16 +208,6 @@ __device__ __forceinline__ int find_bra_in(const long long* __restrict__ off, in
 
 constexpr int kEriThreads = 128;
 
-// Shared-memory staging of the ket primitive records in the FP32 ERI kernels.  A warp's 32 lanes
-// work on 32 different kets, so each lane's loads of its ket records in the primitive loop hit 32
-// different L1 sectors per instruction; the FP32 kernels were bound by that L1 throughput.  The warp
-// instead copies the 32 kets' record blocks with coalesced loads into 32 slots of stride
-// a.stage_stride floats (odd, so equal offsets in different slots fall in different banks) and the
-// primitive loop reads them from shared memory.
-extern __shared__ float kstage_smem[];
-
-inline size_t stage_bytes(int stage_stride, int block) { return (size_t)block * (size_t)stage_stride * sizeof(float); }
-
 // Density-weighted screening: a quartet (AB|CD) changes the six Fock blocks of Eq. 1a-1f by at most
 // Q_AB Q_CD times the largest |P| of the blocks (CD), (AB), (BD), (AC), (BC), (AD) it is contracted with
 // (times 4 for the Coulomb weight); density_block_max returns that largest |P|.  The quartet is skipped
@@ -279,29 +269,12 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
                 live = valid && 4.0f * (float)(hb.Q * hk.Q) * dm >= a.dtau;                                  \
                 pt = ptau / fmaxf(dm, 1e-30f);                                                               \
             }                                                                                                \
-            const PrimPair<real>* kst = nullptr;                                                            \
-            if constexpr (sizeof(real) == 4 && !SOA) {                                                       \
-                if (a.stage_stride > 0) { /* warp-uniform: copy the 32 lanes' ket records */                 \
-                    float* wsm = kstage_smem + (size_t)(threadIdx.x >> 5) * 32 * a.stage_stride;             \
-                    const int wl = threadIdx.x & 31;                                                         \
-                    __syncwarp();                                                                            \
-                    for (int j = 0; j < 32; j++) {                                                           \
-                        const int p0 = __shfl_sync(0xffffffffu, hk.prim0, j);                                \
-                        const int nf = __shfl_sync(0xffffffffu, hk.nprim, j) * (int)(sizeof(PrimPair<float>) / 4); \
-                        const float* src = (const float*)(prims + p0);                                       \
-                        float* dst = wsm + j * a.stage_stride;                                               \
-                        for (int t = wl; t < nf; t += 32) dst[t] = __ldg(src + t);                           \
-                    }                                                                                        \
-                    __syncwarp();                                                                            \
-                    kst = (const PrimPair<real>*)(wsm + wl * a.stage_stride);                                \
-                }                                                                                            \
-            }                                                                                                \
             if constexpr (SOA) {                                                                             \
                 const KetSoa<real> kv{(const real*)a.kt + k, a.ktB + k, a.kstride};                          \
                 nprimq += QFN<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
                                                    live);                                                    \
             } else {                                                                                         \
-                const KetAos<real> kv{kst ? kst : prims + hk.prim0};                                         \
+                const KetAos<real> kv{prims + hk.prim0};                                         \
                 nprimq += QFN<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
                                                    live);                                                    \
             }                                                                                                \
@@ -318,35 +291,21 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
     ERI_KERNEL_BODY(quartet_##NAME)                                                                          \
     void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s, int lanes)   \
     {                                                                                                        \
-        const bool soa = a.kt != nullptr;                                                                    \
-        if (use_f32) {                                                                                       \
-            if (soa)                                                                                         \
-                k_eri_##NAME<float, 1, true><<<grid, block, 0, s>>>(a);                                      \
-            else                                                                                             \
-                k_eri_##NAME<float, 1, false><<<grid, block, stage_bytes(a.stage_stride, block), s>>>(a);   \
-        } else if (lanes > 1) {                                                                              \
-            if (soa)                                                                                         \
-                k_eri_##NAME<double, (GL), true><<<grid, block, 0, s>>>(a);                                  \
-            else                                                                                             \
-                k_eri_##NAME<double, (GL), false><<<grid, block, 0, s>>>(a);                                 \
-        } else {                                                                                             \
-            if (soa)                                                                                         \
-                k_eri_##NAME<double, 1, true><<<grid, block, 0, s>>>(a);                                     \
-            else                                                                                             \
-                k_eri_##NAME<double, 1, false><<<grid, block, 0, s>>>(a);                                    \
-        }                                                                                                    \
+        if (use_f32)                                                                                         \
+            k_eri_##NAME<float, 1, true><<<grid, block, 0, s>>>(a);                                          \
+        else if (lanes > 1)                                                                                  \
+            k_eri_##NAME<double, (GL), false><<<grid, block, 0, s>>>(a);                                     \
+        else                                                                                                 \
+            k_eri_##NAME<double, 1, false><<<grid, block, 0, s>>>(a);                                        \
     }                                                                                                        \
     size_t local_bytes_##NAME()                                                                              \
     {                                                                                                        \
         cudaFuncAttributes fa;                                                                               \
         size_t m = 0;                                                                                        \
         const void* fns[] = {(const void*)k_eri_##NAME<double, 1, false>, (const void*)k_eri_##NAME<double, (GL), false>, \
-                             (const void*)k_eri_##NAME<float, 1, false>, (const void*)k_eri_##NAME<double, 1, true>,   \
-                             (const void*)k_eri_##NAME<double, (GL), true>, (const void*)k_eri_##NAME<float, 1, true>}; \
+                             (const void*)k_eri_##NAME<float, 1, true>, (const void*)k_eri_batch_##NAME};   \
         for (const void* fn : fns)                                                                           \
             if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.localSizeBytes > m) m = fa.localSizeBytes; \
-        if (cudaFuncGetAttributes(&fa, k_eri_batch_##NAME) == cudaSuccess && fa.localSizeBytes > m)          \
-            m = fa.localSizeBytes;                                                                           \
         cudaGetLastError();                                                                                  \
         return m;                                                                                            \
     }

@@ -95,11 +95,17 @@ def vname(e, f, m):
     return f"v{tstr(e)}_{tstr(f)}_{m}"
 
 
-def gen_vrr(la, lb, lc, ld, cnt):
-    """Return (lines, used-coefficient set) for the VRR of one primitive quartet."""
+def all_targets(la, lb, lc, ld):
+    """The contracted-quartet targets [e0|f0]^(0), l_a <= |e| <= l_a + l_b, l_c <= |f| <= l_c + l_d."""
+    return [(e, f, 0) for le in range(la, la + lb + 1) for e in CART[le]
+            for lf in range(lc, lc + ld + 1) for f in CART[lf]]
+
+
+def gen_vrr(la, lb, lc, ld, cnt, subset=None):
+    """Return (lines, accumulation lines, used coefficients, targets) for the VRR of one primitive quartet,
+    restricted to the nodes the targets in `subset` (default: all) need."""
     L = la + lb + lc + ld
-    targets = [(e, f, 0) for le in range(la, la + lb + 1) for e in CART[le]
-               for lf in range(lc, lc + ld + 1) for f in CART[lf]]
+    targets = all_targets(la, lb, lc, ld) if subset is None else subset
     recipe = {}
 
     def need(node):
@@ -184,7 +190,7 @@ def gen_vrr(la, lb, lc, ld, cnt):
 RYS_MIN_L = 6  # classes evaluated by Rys quadrature when asked for (HF_RYS)
 
 
-def gen_rys_prim(la, lb, lc, ld, cnt):
+def gen_rys_prim(la, lb, lc, ld, cnt, subset=None):
     """Rys quadrature replacement of the vertical step for one primitive quartet: with the n = L/2 + 1
     nodes u_r = t_r^2 and weights w_r of the Boys weight at T (rys.cuh), and per node the 2D integrals
     G_d(a, c), d = x, y, z, a <= la + lb, c <= lc + ld, from
@@ -198,8 +204,7 @@ def gen_rys_prim(la, lb, lc, ld, cnt):
     Returns (setup lines, per-primitive body lines, targets, setup flop count)."""
     L = la + lb + lc + ld
     n = L // 2 + 1
-    targets = [(e, f, 0) for le in range(la, la + lb + 1) for e in CART[le]
-               for lf in range(lc, lc + ld + 1) for f in CART[lf]]
+    targets = all_targets(la, lb, lc, ld) if subset is None else subset
     need = [set(), set(), set()]
     for e, f, _ in targets:
         for d in range(3):
@@ -462,9 +467,22 @@ def class_name(X, Y):
     return f"{la}{lb}{lc}{ld}"
 
 
+CHUNK = {8: 96, 4: 192}  # largest number of accumulators per pass over the primitives, by sizeof(real)
+
+
+def target_chunks(targets, size):
+    """Consecutive chunks (targets are ordered by bra component, so a chunk shares its bra recurrence)."""
+    return [targets[i:i + size] for i in range(0, len(targets), size)]
+
+
 def gen_class(X, Y, method="os"):
     """Source of one class's quartet function and kernels: method "os" (Obara-Saika vertical step, Boys
-    table) or "rys" (Rys quadrature vertical step); both share the contraction, HRR and digestion."""
+    table) or "rys" (Rys quadrature vertical step); both share the contraction, HRR and digestion.
+
+    A class with more targets than fit in registers (CHUNK, per arithmetic type) runs its primitive loop
+    in passes, each accumulating one chunk of targets with only the recurrence nodes that chunk needs; the
+    finished chunks are kept in a per-thread array for the horizontal step.  The reported flop counts are
+    those of a single pass over every target (the algorithm's work, not the repeated setup)."""
     la, lb = PAIR_CLASSES[X]
     lc, ld = PAIR_CLASSES[Y]
     L = la + lb + lc + ld
@@ -485,15 +503,80 @@ def gen_class(X, Y, method="os"):
     cont_hrr = cnt.cont
     dig = gen_digest(la, lb, lc, ld, xname, cnt)
     prim_flops = cnt.prim + cset + extra
-    acc_decl = [f"real acc{tstr(e)}_{tstr(f)} = real(0);" for (e, f, m) in targets]
+    tnames = [f"acc{tstr(e)}_{tstr(f)}" for (e, f, m) in targets]
     need_ab = any("AB" in l for l in hrr)
     need_cd = any("CD" in l for l in hrr)
+    G = LANES_BY_L[L]
+
+    def prim_body(chunk):
+        """Lines of one primitive quartet for the targets of `chunk`."""
+        c2 = Counter()
+        if method == "os":
+            v, a_, u, _ = gen_vrr(la, lb, lc, ld, c2, chunk)
+            st, _ = gen_setup(L, u, c2)
+        else:
+            st, v, _, _ = gen_rys_prim(la, lb, lc, ld, c2, chunk)
+            a_, u = [], {"PAx", "PAy", "PAz"}
+        lines = ["const real bK = bp.K, bo2p = bp.oo2p;"]
+        lines += [f"const real PA{x} = bp.PA{x};" for x in AX if f"PA{x}" in u]
+        lines += st
+        # each target is accumulated right after its recurrence node, which keeps fewer values alive
+        acc_of = {l.split(" += ")[1].rstrip(";"): l for l in a_}
+        for l in v:
+            lines.append(l)
+            if l.startswith("const real v"):
+                nm = l.split(" = ")[0].split()[-1]
+                if nm in acc_of:
+                    lines.append(acc_of.pop(nm))
+        lines += list(acc_of.values())
+        return lines
+
+    def pass_lines(chunk, first, store):
+        """One pass over the primitive staircase accumulating `chunk`."""
+        cn = [f"acc{tstr(e)}_{tstr(f)}" for (e, f, m) in chunk]
+        o = ["{"]
+        o += [f"    real {nm} = real(0);" for nm in cn]
+        o.append("    // lane l evaluates staircase positions l, l + G, l + 2G, ... in lockstep with its group")
+        o.append("    int nkb = nkb0, ib = 0, ik = 0;")
+        o.append("    auto advance = [&]() {")
+        o.append("        if (++ik == nkb) {")
+        o.append("            ik = 0;")
+        o.append("            ib++;")
+        o.append("            if (ib < nbp)")
+        o.append("                while (nkb > 0 && bpp[ib].B * kv.B(nkb - 1) < ptau) nkb--;")
+        o.append("        }")
+        o.append("    };")
+        o.append("    if (G > 1)")
+        o.append("        for (int s = 0; s < lane && s < total; s++) advance();")
+        o.append("    for (int it = (G > 1 ? lane : 0); it < total; it += G) {")
+        o.append("        const int cib = ib, cik = ik;")
+        o.append("#pragma unroll")
+        o.append("        for (int s = 0; s < G; s++) advance();")
+        if first:
+            o.append("        nq++;")
+        o.append("        const PrimPair<real> bp = bpp[cib];")
+        o.append("        const PrimPair<real> kp = kv.rec(cik);")
+        o += ["        " + l for l in prim_body(chunk)]
+        o.append("    }")
+        o.append("    if constexpr (G > 1) {")
+        o.append("#pragma unroll")
+        o.append("        for (int o = 1; o < G; o <<= 1) {")
+        o += [f"            {nm} += __shfl_xor_sync(0xffffffffu, {nm}, o);" for nm in cn]
+        o.append("        }")
+        o.append("    }")
+        if store:
+            o += [f"    accv[{tnames.index(nm)}] = {nm};" for nm in cn]
+        o.append("}")
+        return o
+
+    ch = {sz: target_chunks(targets, CHUNK[sz]) for sz in (8, 4)}
+    chunked = len(ch[8]) > 1 or len(ch[4]) > 1
 
     out = []
     out.append(f"// ({PAIR_NAMES[X]}|{PAIR_NAMES[Y]}) class: l = {la}{lb}{lc}{ld}, "
                f"{len(targets)} [e0|f0] targets, {prim_flops} flops per primitive quartet, "
-               f"{cnt.cont} per contracted quartet" + (", Rys quadrature." if method == "rys" else "."))
-    G = LANES_BY_L[L]
+               f"{cnt.cont} per contracted quartet" + (", Rys quadrature" if method == "rys" else "")
+               + (f"; {len(ch[8])} passes in FP64, {len(ch[4])} in FP32." if chunked else "."))
     out.append(f"// Lanes per quartet in the ERI kernels: {G}.  The G lanes of a group share one shell quartet's")
     out.append(f"// primitive staircase round-robin and sum their accumulators with butterfly shuffles; lane 0")
     out.append(f"// then runs the horizontal recurrence and the digestion.  Called warp-uniformly; a lane with")
@@ -509,58 +592,30 @@ def gen_class(X, Y, method="os"):
     out.append("    // kv: the ket's records (KetAos: the pair's record array; KetSoa: its column of the class's ket table)")
     out.append("    const PrimPair<real>* __restrict__ bpp = prims + hb.prim0;")
     out.append("    const int nbp = hb.nprim;")
-    out.append("    int nkb = hk.nprim;")
+    out.append("    int nkb0 = hk.nprim;")
     out.append("    int total = 0;")
     out.append("    if (valid) {")
-    out.append("        for (int ib = 0, c = nkb; ib < nbp; ib++) {")
+    out.append("        for (int ib = 0, c = nkb0; ib < nbp; ib++) {")
     out.append("            const float Bb = bpp[ib].B;")
     out.append("            while (c > 0 && Bb * kv.B(c - 1) < ptau) c--;")
     out.append("            if (c == 0) break;")
     out.append("            total += c;")
     out.append("        }")
-    out.append("        while (nkb > 0 && bpp[0].B * kv.B(nkb - 1) < ptau) nkb--;")
+    out.append("        while (nkb0 > 0 && bpp[0].B * kv.B(nkb0 - 1) < ptau) nkb0--;")
     out.append("    }")
     out.append("    int nq = 0;")
-    for l in acc_decl:
-        out.append("    " + l)
-    out.append("    // lane l evaluates staircase positions l, l + G, l + 2G, ... in lockstep with its group")
-    out.append("    int ib = 0, ik = 0;")
-    out.append("    auto advance = [&]() {")
-    out.append("        if (++ik == nkb) {")
-    out.append("            ik = 0;")
-    out.append("            ib++;")
-    out.append("            if (ib < nbp)")
-    out.append("                while (nkb > 0 && bpp[ib].B * kv.B(nkb - 1) < ptau) nkb--;")
-    out.append("        }")
-    out.append("    };")
-    out.append("    if (G > 1)")
-    out.append("        for (int s = 0; s < lane && s < total; s++) advance();")
-    out.append("    for (int it = (G > 1 ? lane : 0); it < total; it += G) {")
-    out.append("        const int cib = ib, cik = ik;")
-    out.append("#pragma unroll")
-    out.append("        for (int s = 0; s < G; s++) advance();")
-    out.append("        nq++;")
-    out.append("        const PrimPair<real> bp = bpp[cib];")
-    out.append("        const PrimPair<real> kp = kv.rec(cik);")
-    out.append("        const real bK = bp.K, bo2p = bp.oo2p;")
-    for a in AX:
-        if f"PA{a}" in used:
-            out.append(f"        const real PA{a} = bp.PA{a};")
-    for l in setup:
-        out.append("        " + l)
-    for l in vrr:
-        out.append("        " + l)
-    for l in acc:
-        out.append("        " + l)
-    out.append("    }")
-    out.append("    if constexpr (G > 1) {")
-    out.append("#pragma unroll")
-    out.append("        for (int o = 1; o < G; o <<= 1) {")
-    for (e, f, m) in targets:
-        nm = f"acc{tstr(e)}_{tstr(f)}"
-        out.append(f"            {nm} += __shfl_xor_sync(0xffffffffu, {nm}, o);")
-    out.append("        }")
-    out.append("    }")
+    if not chunked:
+        p_ = pass_lines(targets, True, False)
+        # single pass: its accumulators stay in scope for the horizontal step
+        out += ["    " + l for l in p_[1:-1]]
+    else:
+        out.append(f"    real accv[{len(targets)}];  // finished chunks of targets")
+        for sz, kw in ((8, "if constexpr (sizeof(real) == 8)"), (4, "else")):
+            out.append(f"    {kw} {{")
+            for k, c in enumerate(ch[sz]):
+                out += ["        " + l for l in pass_lines(c, k == 0, True)]
+            out.append("    }")
+        out += [f"    const real {nm} = accv[{i}];" for i, nm in enumerate(tnames)]
     out.append("    if (!valid || lane != 0) return nq;")
     tail = []
     if need_ab:

@@ -52,13 +52,12 @@ struct EriArgs {
     float dtau;                       // density-weighted screening threshold
     const int* chunk;                 // [c] bra of quartet min(c << kChunkShift, n_quartets_all - 1)
                                       // (nullptr: each quartet's bra by binary search over all bras)
-    int stage_stride;                 // FP32 launches: floats per lane of the shared-memory ket staging
-                                      // (0: ket records read from global memory)
     int n_copies;                     // > 1: block b accumulates into copy b % n_copies of Jt / Kt
     long long copy_stride;            // doubles between copies
     const int* bad;                   // density-check flag: the kernel does nothing when *bad != 0
     const void* kt;                   // ket table of the launch's ket class and precision (field-major records
-                                      // in class-list order, see KetSoa); nullptr: records read per pair
+                                      // in class-list order, see KetSoa): read by the FP32 and Rys kernels; the
+                                      // FP64 Obara-Saika kernels read each pair's own records
     const float* ktB;                 // primitive-pair bounds of the ket table
     long long kstride;                // kets per field row of the ket table
 };
@@ -217,7 +216,6 @@ struct hf_system {
     // field-major (9 maxpp rows of FP64 fields, 9 maxpp rows of FP32 fields, maxpp rows of bounds)
     hf::DevBuf ket_tab[hf::kNumPairClasses];
     long long ket_stride[hf::kNumPairClasses] = {};
-    bool ket_soa = true;  // ERI launches read ket records from the ket tables
     int fock_copies = 1;                           // accumulator copies of Jt / Kt (1: one shared copy)
     hf::DevBuf copies;                             // [2][fock_copies][N*N] when fock_copies > 1
     int maxpp = 0;
