@@ -140,7 +140,16 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
         need(t)
     order = sorted(recipe.keys(), key=lambda n: (sum(n[0]) + sum(n[1]), sum(n[1]), -n[2]))
     used = set()
+    # targets no other node depends on are accumulated as an FMA chain of their recurrence terms
+    # (acc = fma(c_k, x_k, acc) per term) instead of forming their value and adding it
+    depended = set()
+    for node, r in recipe.items():
+        if r[0] != "base":
+            depended.update(r[-1])
+    tset = set(targets)
+    leaf = {n for n in tset if n not in depended and recipe[n][0] != "base"}
     lines = []
+    acc = []
     for node in order:
         e, f, m = node
         r = recipe[node]
@@ -151,38 +160,43 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
             continue
         i = r[1]
         a = AX[i]
+        terms = []  # (coefficient, operand)
         if r[0] == "e1":
             e1 = sub(e, i)
-            expr = f"PA{a} * {vname(e1, Z3, m)} + WP{a} * {vname(e1, Z3, m + 1)}"
+            terms += [(f"PA{a}", vname(e1, Z3, m)), (f"WP{a}", vname(e1, Z3, m + 1))]
             used.update({f"PA{a}", f"WP{a}"})
             cnt.prim += 3
             if e[i] >= 2:
                 e2 = sub(e, i, 2)
                 k = e[i] - 1
-                expr += f" + o2p_{k} * ({vname(e2, Z3, m)} - rho_p * {vname(e2, Z3, m + 1)})"
+                terms.append((f"o2p_{k}", f"({vname(e2, Z3, m)} - rho_p * {vname(e2, Z3, m + 1)})"))
                 used.update({f"o2p_{k}", "rho_p"})
                 cnt.prim += 4
-            lines.append(f"const real {nm} = {expr};")
         else:
             f1 = sub(f, i)
-            expr = f"QC{a} * {vname(e, f1, m)} + WQ{a} * {vname(e, f1, m + 1)}"
+            terms += [(f"QC{a}", vname(e, f1, m)), (f"WQ{a}", vname(e, f1, m + 1))]
             used.update({f"QC{a}", f"WQ{a}"})
             cnt.prim += 3
             if f[i] >= 2:
                 f2 = sub(f, i, 2)
                 k = f[i] - 1
-                expr += f" + o2q_{k} * ({vname(e, f2, m)} - rho_q * {vname(e, f2, m + 1)})"
+                terms.append((f"o2q_{k}", f"({vname(e, f2, m)} - rho_q * {vname(e, f2, m + 1)})"))
                 used.update({f"o2q_{k}", "rho_q"})
                 cnt.prim += 4
             if e[i] >= 1:
                 k = e[i]
-                expr += f" + o2pq_{k} * {vname(sub(e, i), f1, m + 1)}"
+                terms.append((f"o2pq_{k}", vname(sub(e, i), f1, m + 1)))
                 used.add(f"o2pq_{k}")
                 cnt.prim += 2
-            lines.append(f"const real {nm} = {expr};")
-    acc = []
+        if node in leaf:
+            an = f"acc{tstr(e)}_{tstr(f)}"
+            for c, x in terms:
+                lines.append(f"{an} = fma({c}, {x}, {an});")
+        else:
+            lines.append(f"const real {nm} = " + " + ".join(f"{c} * {x}" for c, x in terms) + ";")
     for (e, f, m) in targets:
-        acc.append(f"acc{tstr(e)}_{tstr(f)} += {vname(e, f, 0)};")
+        if (e, f, m) not in leaf:
+            acc.append(f"acc{tstr(e)}_{tstr(f)} += {vname(e, f, 0)};")
         cnt.prim += 1
     return lines, acc, used, targets
 
