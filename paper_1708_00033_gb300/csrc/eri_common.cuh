@@ -179,6 +179,31 @@ __device__ __forceinline__ void boys(real T, const real* __restrict__ tab, real*
 
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
 
+// FP64 value of an FP32 number by integer operations (sign, exponent rebiased by 1023 - 127, mantissa
+// shifted into the high word): exact for normal numbers, +-0 for zeros and subnormals (|x| < 1.2e-38), and
+// infinities and NaNs kept.  The FP32 kernels widen every digested value this way, so that they issue no
+// instruction on the FP64 pipe, which runs at 1/64 of the FP32 rate on this GPU.
+__device__ __forceinline__ double widen(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned ee = e == 0xffu ? 0x7ffu : e + 896u;
+    const unsigned hi = e == 0u ? (u & 0x80000000u) : ((u & 0x80000000u) | (ee << 20) | ((u & 0x7fffffu) >> 3));
+    const unsigned lo = e == 0u ? 0u : (u << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
+// A - B of a pair in the kernel's arithmetic type (FP32 kernels read the FP32 copies).
+template <typename real>
+__device__ __forceinline__ real pair_ab(double d, float f)
+{
+    if constexpr (sizeof(real) == 8)
+        return d;
+    else
+        return f;
+}
+
 // Largest b in [0, n) with off[b] <= q (off is non-decreasing, off[0] = 0).
 __device__ __forceinline__ int find_bra(const long long* __restrict__ off, int n, long long q)
 {
@@ -247,7 +272,7 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
             const long long q = wb + grp;                                                                    \
             const bool valid = q < a.n_quartets;                                                             \
             PairHdr hb, hk;                                                                                  \
-            double f = 1.0;                                                                                  \
+            real f = real(1);                                                                                \
             int k = 0;                                                                                       \
             if (valid) {                                                                                     \
                 const long long c = q >> kChunkShift;                                                        \
@@ -256,9 +281,9 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
                 k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                                  \
                 hb = a.pairs[a.bra[b]];                                                                      \
                 hk = a.pairs[a.ket[k]];                                                                      \
-                if (hb.A == hb.B) f *= 0.5;                                                                  \
-                if (hk.A == hk.B) f *= 0.5;                                                                  \
-                if (a.same && b == k) f *= 0.5;                                                              \
+                if (hb.A == hb.B) f *= real(0.5);                                                            \
+                if (hk.A == hk.B) f *= real(0.5);                                                            \
+                if (a.same && b == k) f *= real(0.5);                                                        \
             } else {                                                                                         \
                 hb = hk = a.pairs[a.bra[0]];                                                                 \
             }                                                                                                \

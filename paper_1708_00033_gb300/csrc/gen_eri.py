@@ -442,7 +442,7 @@ def gen_digest(la, lb, lc, ld, xname, cnt):
                 ts = terms(u, v)
                 expr = " + ".join(f"{xx} * {pp}" for xx, pp in ts)
                 cnt.cont += 2 * len(ts) + 1
-                lines.append(f"red_add(&{target}[(size_t)({r0} + {u}) * N + {c0} + {v}], (double)({scale} * ({expr})));")
+                lines.append(f"red_add(&{target}[(size_t)({r0} + {u}) * N + {c0} + {v}], widen({scale} * ({expr})));")
 
     block("Jt", "bA", na, "bB", nb, lambda a, b: [(x(a, b, c, d), f"Pcd_{c}_{d}") for c in range(nc) for d in range(nd)], "fj")
     block("Jt", "bC", nc, "bD", nd, lambda c, d: [(x(a, b, c, d), f"Pab_{a}_{b}") for a in range(na) for b in range(nb)], "fj")
@@ -481,7 +481,11 @@ def class_name(X, Y):
     return f"{la}{lb}{lc}{ld}"
 
 
-CHUNK = {8: 96, 4: 192}  # largest number of accumulators per pass over the primitives, by sizeof(real)
+# Largest number of accumulators per pass over the primitives, by sizeof(real).  FP32 classes with more
+# targets run in passes (measured: (dd|dp) 43 -> 10.5 ms, (dd|dd) 15 -> 10 ms at 64 waters); the FP64
+# kernels, bound by the FP64 pipe, lost more to the repeated setup than they gained from fewer spills
+# ((dp|dp) +17%, (dd|dd) +42%), so they run in one pass.
+CHUNK = {8: 10 ** 9, 4: 192}
 
 
 def target_chunks(targets, size):
@@ -598,7 +602,7 @@ def gen_class(X, Y, method="os"):
     out.append(f"template <typename real, int G, typename KV>")
     out.append(f"__device__ __forceinline__ int {qname}(const PairHdr& hb, const PairHdr& hk, const KV& kv,"
                f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
-    out.append(f"    const real* __restrict__ Pd, int N, double fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
+    out.append(f"    const real* __restrict__ Pd, int N, real fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
     out.append(f"    float ptau, int lane, bool valid)")
     out.append("{")
     out.append("    // surviving primitive quartets form a staircase (pairs sorted by bound): bra primitive ib")
@@ -633,9 +637,11 @@ def gen_class(X, Y, method="os"):
     out.append("    if (!valid || lane != 0) return nq;")
     tail = []
     if need_ab:
-        tail.append("const real ABx = (real)hb.ABx, ABy = (real)hb.ABy, ABz = (real)hb.ABz;")
+        tail.append("const real ABx = pair_ab<real>(hb.ABx, hb.ABfx), ABy = pair_ab<real>(hb.ABy, hb.ABfy), "
+                    "ABz = pair_ab<real>(hb.ABz, hb.ABfz);")
     if need_cd:
-        tail.append("const real CDx = (real)hk.ABx, CDy = (real)hk.ABy, CDz = (real)hk.ABz;")
+        tail.append("const real CDx = pair_ab<real>(hk.ABx, hk.ABfx), CDy = pair_ab<real>(hk.ABy, hk.ABfy), "
+                    "CDz = pair_ab<real>(hk.ABz, hk.ABfz);")
     tail += hrr
     tail.append("if (qout) {")
     if X == Y:
@@ -645,7 +651,7 @@ def gen_class(X, Y, method="os"):
     tail.append("}")
     tail.append("if (total == 0) return;  // every primitive quartet screened: nothing to digest")
     tail.append("const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
-    tail.append("const real fj = (real)(4.0 * fscale), fk = (real)(2.0 * fscale);")
+    tail.append("const real fj = real(4) * fscale, fk = real(2) * fscale;")
     tail += dig
     out += ["    " + l.replace("return;", "return nq;") for l in tail]
     out.append("    return nq;")

@@ -24,6 +24,7 @@ struct PairHdr {
     int prim0, nprim;  // primitive-pair records [prim0, prim0 + nprim)
     double ABx, ABy, ABz;
     double Q;          // Cauchy-Schwarz bound sqrt(max |(mu nu|mu nu)|)
+    float ABfx, ABfy, ABfz;  // A - B in FP32 (the FP32 kernels' horizontal step uses no FP64 instruction)
 };
 
 struct EriArgs {

@@ -139,6 +139,9 @@ __global__ void k_build_pairs(long long n_pairs, int maxpp, const int* __restric
     h.ABy = ABy;
     h.ABz = ABz;
     h.Q = 0.0;
+    h.ABfx = (float)ABx;
+    h.ABfy = (float)ABy;
+    h.ABfz = (float)ABz;
     pairs[t] = h;
     pclass[t] = la * (la + 1) / 2 + lb;
     const double c52 = sqrt(2.0) * pow(M_PI, 1.25);  // sqrt(2) pi^(5/4)
