@@ -197,21 +197,6 @@ __device__ __forceinline__ void boys(real T, const real* __restrict__ tab, real*
 
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
 
-// FP64 value of an FP32 number by integer operations (sign, exponent rebiased by 1023 - 127, mantissa
-// shifted into the high word): exact for normal numbers, +-0 for zeros and subnormals (|x| < 1.2e-38), and
-// infinities and NaNs kept.  The FP32 kernels widen every digested value this way, so that they issue no
-// instruction on the FP64 pipe, which runs at 1/64 of the FP32 rate on this GPU.
-__device__ __forceinline__ double widen(float x)
-{
-    const unsigned u = __float_as_uint(x);
-    const unsigned e = (u >> 23) & 0xffu;
-    const unsigned ee = e == 0xffu ? 0x7ffu : e + 896u;
-    const unsigned hi = e == 0u ? (u & 0x80000000u) : ((u & 0x80000000u) | (ee << 20) | ((u & 0x7fffffu) >> 3));
-    const unsigned lo = e == 0u ? 0u : (u << 29);
-    return __hiloint2double((int)hi, (int)lo);
-}
-__device__ __forceinline__ double widen(double x) { return x; }
-
 // A - B of a pair in the kernel's arithmetic type (FP32 kernels read the FP32 copies).
 template <typename real>
 __device__ __forceinline__ real pair_ab(double d, float f)

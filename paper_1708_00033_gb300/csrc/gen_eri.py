@@ -443,7 +443,7 @@ def gen_digest(la, lb, lc, ld, xname, cnt):
                 ts = terms(u, v)
                 expr = " + ".join(f"{xx} * {pp}" for xx, pp in ts)
                 cnt.cont += 2 * len(ts) + 1
-                lines.append(f"red_add(&{target}[(size_t)({r0} + {u}) * N + {c0} + {v}], widen({scale} * ({expr})));")
+                lines.append(f"red_add(&{target}[(size_t)({r0} + {u}) * N + {c0} + {v}], (double)({scale} * ({expr})));")
 
     block("Jt", "bA", na, "bB", nb, lambda a, b: [(x(a, b, c, d), f"Pcd_{c}_{d}") for c in range(nc) for d in range(nd)], "fj")
     block("Jt", "bC", nc, "bD", nd, lambda c, d: [(x(a, b, c, d), f"Pab_{a}_{b}") for a in range(na) for b in range(nb)], "fj")
