@@ -453,6 +453,9 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
         float* tB = t32 + 9 * rows * stride;
         KCHK(launch_ket_table(n, X.maxpp, stride, S->class_ids[c].as<int>(), S->pairs.as<PairHdr>(), S->prims64.p,
                               S->prims32.p, t64, t32, tB, st));
+        TRY(S->class_hdr[c].alloc(sizeof(PairHdr) * (size_t)n));
+        KCHK(launch_gather_headers(n, S->class_ids[c].as<int>(), S->pairs.as<PairHdr>(), S->class_hdr[c].as<PairHdr>(),
+                                   st));
     }
     // bra lookup tables (their sizes follow from the quartet totals)
     for (int ci = 0; ci < kNumClasses; ci++) {
@@ -615,7 +618,8 @@ int hf_system_get_info(const hf_system* S, hf_system_info* info)
                             &S->pair_class, &S->S, &S->H, &S->P64, &S->P32, &S->Jt, &S->Kt, &S->F, &S->Ebuf,
                             &S->Qall, &S->staging_P, &S->staging_out};
     for (auto* b : bufs) bytes += b->bytes;
-    for (int c = 0; c < kNumPairClasses; c++) bytes += S->class_ids[c].bytes + S->class_q[c].bytes + S->ket_tab[c].bytes;
+    for (int c = 0; c < kNumPairClasses; c++)
+        bytes += S->class_ids[c].bytes + S->class_q[c].bytes + S->ket_tab[c].bytes + S->class_hdr[c].bytes;
     for (int c = 0; c < kNumClasses; c++)
         bytes += S->plan[c].offsets64.bytes + S->plan[c].offsets32.bytes + S->plan[c].kstart32.bytes +
                  S->plan[c].chunk64.bytes + S->plan[c].chunk32.bytes;
@@ -721,6 +725,8 @@ int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int
         const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
         a.bra = S->class_ids[Xc].as<int>();
         a.ket = S->class_ids[Yc].as<int>();
+        a.bhdr = S->class_hdr[Xc].as<PairHdr>();
+        a.khdr = S->class_hdr[Yc].as<PairHdr>();
         a.n_bra = S->class_count[Xc];
         a.same = Xc == Yc;
         for (int prec = 0; prec < 2; prec++) {

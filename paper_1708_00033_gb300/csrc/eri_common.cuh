@@ -282,13 +282,13 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
                 const int b = a.chunk ? find_bra_in(a.offsets, a.chunk[c], a.chunk[c + 1], q)                 \
                                       : find_bra(a.offsets, a.n_bra, q);                                     \
                 k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                                  \
-                hb = a.pairs[a.bra[b]];                                                                      \
-                hk = a.pairs[a.ket[k]];                                                                      \
+                hb = a.bhdr[b];                                                                              \
+                hk = a.khdr[k];                                                                              \
                 if (hb.A == hb.B) f *= real(0.5);                                                            \
                 if (hk.A == hk.B) f *= real(0.5);                                                            \
                 if (a.same && b == k) f *= real(0.5);                                                        \
             } else {                                                                                         \
-                hb = hk = a.pairs[a.bra[0]];                                                                 \
+                hb = hk = a.bhdr[0];                                                                         \
             }                                                                                                \
             bool live = valid;                                                                               \
             float pt = ptau;                                                                                 \
@@ -366,8 +366,8 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
             const bool valid = lane < count;                                                                 \
             const int2 e = valid ? qu[base + lane] : make_int2(0, 0);                                        \
             __syncwarp();                                                                                    \
-            const PairHdr hb = a.pairs[a.bra[e.x]];                                                          \
-            const PairHdr hk = a.pairs[a.ket[e.y]];                                                          \
+            const PairHdr hb = a.bhdr[e.x];                                                                  \
+            const PairHdr hk = a.khdr[e.y];                                                                  \
             double f = 1.0;                                                                                  \
             if (hb.A == hb.B) f *= 0.5;                                                                      \
             if (hk.A == hk.B) f *= 0.5;                                                                      \

@@ -70,6 +70,8 @@ struct EriArgs {
     const float* ktB;                 // primitive-pair bounds of the ket table
     long long kstride;                // kets per field row of the ket table
     const PairGeo* pgeo;              // [pair id] centre intervals (far/near kernels)
+    const PairHdr* bhdr;              // headers of the bra list in list order (bhdr[b] = pairs[bra[b]])
+    const PairHdr* khdr;              // headers of the ket list in list order (khdr[k] = pairs[ket[k]])
 };
 
 struct SchwarzArgs {
@@ -227,6 +229,7 @@ struct hf_system {
     // ket tables: per pair class, the significant pairs' primitive-pair records in class-list order and
     // field-major (9 maxpp rows of FP64 fields, 9 maxpp rows of FP32 fields, maxpp rows of bounds)
     hf::DevBuf ket_tab[hf::kNumPairClasses];
+    hf::DevBuf class_hdr[hf::kNumPairClasses];  // pair headers of each class list, in list order
     long long ket_stride[hf::kNumPairClasses] = {};
     int fock_copies = 1;                           // accumulator copies of Jt / Kt (1: one shared copy)
     hf::DevBuf copies;                             // [2][fock_copies][N*N] when fock_copies > 1

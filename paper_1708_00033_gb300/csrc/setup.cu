@@ -343,6 +343,20 @@ __global__ void k_ket_table(int n, int maxpp, long long stride, const int* __res
     tB[(long long)i * stride + k] = i < h.nprim ? r.B : 0.0f;
 }
 
+// out[k] = pairs[ids[k]]: a class list's pair headers in list order
+__global__ void k_gather_headers(int n, const int* __restrict__ ids, const PairHdr* __restrict__ pairs,
+                                 PairHdr* __restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = pairs[ids[k]];
+}
+
+int launch_gather_headers(int n, const int* ids, const PairHdr* pairs, PairHdr* out, cudaStream_t s)
+{
+    if (n > 0) k_gather_headers<<<(n + 255) / 256, 256, 0, s>>>(n, ids, pairs, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_ket_table(int n, int maxpp, long long stride, const int* ids, const PairHdr* pairs, const void* p64,
                      const void* p32, double* t64, float* t32, float* tB, cudaStream_t s)
 {

@@ -19,6 +19,7 @@ int launch_copy_q(long long n, const double* Q, PairHdr* pairs, unsigned long lo
 int launch_class_scatter_sig(long long n, const int* pclass, const double* Q, int X, double qmax, double tau,
                              unsigned* cursor, double* key, int* val, cudaStream_t s);
 int bitonic_sort_desc(double* key, int* val, int n, int n_pad, cudaStream_t s);
+int launch_gather_headers(int n, const int* ids, const PairHdr* pairs, PairHdr* out, cudaStream_t s);
 int launch_ket_table(int n, int maxpp, long long stride, const int* ids, const PairHdr* pairs, const void* p64,
                      const void* p32, double* t64, float* t32, float* tB, cudaStream_t s);
 int launch_sort_prims(long long n_pairs, const PairHdr* pairs, const double* Bprim, void* p64, void* p32, cudaStream_t s);
