@@ -293,7 +293,6 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
     a1.add(S->prims64, sizeof(PrimPair<double>) * npairs * X.maxpp);
     a1.add(S->prims32, sizeof(PrimPair<float>) * npairs * X.maxpp);
     a1.add(S->pair_class, sizeof(int) * npairs);
-    a1.add(S->pair_geo, sizeof(PairGeo) * npairs);
     a1.add(X.counts, sizeof(unsigned long long) * 16);
     a1.add(X.Qall, sizeof(double) * npairs);
     a1.add(X.Bprim, sizeof(double) * npairs * X.maxpp);
@@ -333,7 +332,7 @@ static int system_setup(hf_system* S, const hf_geometry* geom, const hf_basis* b
     KCHK(launch_build_pairs(npairs, X.maxpp, S->sh_l.as<int>(), S->sh_atom.as<int>(), S->sh_bf0.as<int>(),
                             S->sh_nprim.as<int>(), S->sh_prim0.as<int>(), S->sh_exp.as<double>(),
                             S->sh_coef.as<double>(), S->atom_xyz.as<double>(), S->pairs.as<PairHdr>(),
-                            S->prims64.p, S->prims32.p, S->pair_class.as<int>(), S->pair_geo.as<PairGeo>(), st));
+                            S->prims64.p, S->prims32.p, S->pair_class.as<int>(), st));
     unsigned long long* cnt_dev = X.counts.as<unsigned long long>();  // [0..5] class counts, [8..15] cursors
     HF_CUDA(cudaMemsetAsync(cnt_dev, 0, sizeof(unsigned long long) * 16, st));
     KCHK(launch_class_count(npairs, S->pair_class.as<int>(), cnt_dev, st));
@@ -719,7 +718,6 @@ int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int
     a.boys64 = ctx->boys64.as<double>();
     a.boys32 = ctx->boys32.as<float>();
     a.prim_tau = S->th.prim_tau;
-    a.pgeo = S->pair_geo.as<PairGeo>();
     for (int ci = 0; ci < kNumClasses; ci++) {
         const auto& pl = S->plan[ci];
         const int Xc = kEriClasses[ci].X, Yc = kEriClasses[ci].Y;
@@ -759,8 +757,6 @@ int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int
                 const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
                 if (uses_rys(ci, flags, use_f32, a))
                     kEriClasses[ci].launch_rys(a, 0, grid, kEriThreads, st, lanes);
-                else if (!use_f32 && lanes == 1 && !a.dsh && kEriClasses[ci].launch_fn)
-                    kEriClasses[ci].launch_fn(a, grid, kEriThreads, st);  // far/near queues
                 else
                     kEriClasses[ci].launch(a, use_f32, grid, kEriThreads, st, lanes);
                 HF_CUDA(cudaGetLastError());

@@ -11,8 +11,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <type_traits>
-
 #include "hf_internal.h"
 
 namespace hf {
@@ -173,26 +171,10 @@ __device__ __forceinline__ void boys_eval(float T, const float* __restrict__ tab
     }
 }
 
-// The asymptotic form alone, for quartets known to have T >= the switch point in every primitive quartet.
-template <int L, typename real>
-__device__ __forceinline__ void boys_asym(real T, real* F)
-{
-    const real rs = rsq(T);
-    F[0] = real(0.88622692545275801365) * rs;
-    if constexpr (L > 0) {
-        const real h = real(0.5) * rs * rs;
-#pragma unroll
-        for (int m = 0; m < L; m++) F[m + 1] = F[m] * (real(2 * m + 1) * h);
-    }
-}
-
-template <typename real, int L, bool FAR = false>
+template <typename real, int L>
 __device__ __forceinline__ void boys(real T, const real* __restrict__ tab, real* F)
 {
-    if constexpr (FAR)
-        boys_asym<L>(T, F);
-    else
-        boys_eval<L>(T, tab, F);
+    boys_eval<L>(T, tab, F);
 }
 
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
@@ -336,94 +318,6 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
             if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.localSizeBytes > m) m = fa.localSizeBytes; \
         cudaGetLastError();                                                                                  \
         return m;                                                                                            \
-    }
-
-// Far/near variant of a low-L class (FP64, one lane per quartet, no density screening).  Each warp reads
-// its next 32 quartets, bounds each one's smallest Boys argument from the pairs' centre intervals
-// (T >= rho_min d^2, rho_min = pmin_ab pmin_cd / (pmin_ab + pmin_cd), d = the distance of the two centre
-// intervals), and pushes it onto a near or a far queue in shared memory; whenever a queue holds 32
-// quartets the warp evaluates them together, the far ones with the asymptotic Boys form only.  So a warp
-// does not run both Boys branches for the far quartets (those whose every primitive quartet has
-// T >= boys_switch64(L)), which would otherwise be mixed with near ones.
-#define ERI_FARNEAR_KERNEL(NAME, LTOT)                                                                       \
-    __global__ void __launch_bounds__(kEriThreads) k_eri_fn_##NAME(const EriArgs a)                         \
-    {                                                                                                        \
-        if (a.bad && *a.bad) return;                                                                         \
-        const PrimPair<double>* prims = (const PrimPair<double>*)a.prims64;                                  \
-        const float ptau = (float)a.prim_tau;                                                                \
-        const size_t cofs = a.n_copies > 1 ? (size_t)(blockIdx.x % a.n_copies) * a.copy_stride : 0;          \
-        double* const Jt = a.Jt + cofs;                                                                      \
-        double* const Kt = a.Kt + cofs;                                                                      \
-        __shared__ int2 fn_queue[kEriThreads / 32][2][64];                                                   \
-        const int lane = threadIdx.x & 31;                                                                   \
-        int2* const qn = fn_queue[threadIdx.x >> 5][0];                                                      \
-        int2* const qf = fn_queue[threadIdx.x >> 5][1];                                                      \
-        int nn = 0, nf = 0; /* warp-uniform queue lengths */                                                 \
-        unsigned nprimq = 0;                                                                                 \
-        const float tsw = (float)boys_switch64(LTOT) * 1.001f;                                               \
-        const unsigned lt = (1u << lane) - 1u;                                                               \
-        auto run = [&](const int2* qu, int base, int count, auto far_tag) {                                  \
-            const bool valid = lane < count;                                                                 \
-            const int2 e = valid ? qu[base + lane] : make_int2(0, 0);                                        \
-            __syncwarp();                                                                                    \
-            const PairHdr hb = a.bhdr[e.x];                                                                  \
-            const PairHdr hk = a.khdr[e.y];                                                                  \
-            double f = 1.0;                                                                                  \
-            if (hb.A == hb.B) f *= 0.5;                                                                      \
-            if (hk.A == hk.B) f *= 0.5;                                                                      \
-            if (a.same && e.x == e.y) f *= 0.5;                                                              \
-            nprimq += quartet_##NAME<double, 1, KetAos<double>, decltype(far_tag)::value>(                   \
-                hb, hk, KetAos<double>{prims + hk.prim0}, prims, a.boys64, a.P64, a.N, f, Jt, Kt, nullptr, ptau,  \
-                0, valid);                                                                                   \
-        };                                                                                                   \
-        const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                      \
-        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;                                   \
-        for (long long wb = a.q_begin + warp * 32; wb < a.n_quartets; wb += nwarps * 32) { /* warp-uniform */   \
-            const long long q = wb + lane;                                                                   \
-            const bool valid = q < a.n_quartets;                                                             \
-            int b = 0, k = 0;                                                                                \
-            bool far = false;                                                                                \
-            if (valid) {                                                                                     \
-                const long long c = q >> kChunkShift;                                                        \
-                b = a.chunk ? find_bra_in(a.offsets, a.chunk[c], a.chunk[c + 1], q)                          \
-                            : find_bra(a.offsets, a.n_bra, q);                                               \
-                k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                                  \
-                const PairGeo gb = a.pgeo[a.bra[b]], gk = a.pgeo[a.ket[k]];                                  \
-                const float dx = gb.cx - gk.cx, dy = gb.cy - gk.cy, dz = gb.cz - gk.cz;                      \
-                const float d = sqrtf(dx * dx + dy * dy + dz * dz) - gb.r - gk.r - 1e-3f;                    \
-                const float rho = gb.pmin * gk.pmin / (gb.pmin + gk.pmin);                                   \
-                far = d > 0.0f && rho * d * d >= tsw;                                                        \
-            }                                                                                                \
-            const unsigned mf = __ballot_sync(0xffffffffu, valid && far);                                   \
-            const unsigned mn = __ballot_sync(0xffffffffu, valid && !far);                                  \
-            if (valid) {                                                                                     \
-                if (far)                                                                                     \
-                    qf[nf + __popc(mf & lt)] = make_int2(b, k);                                              \
-                else                                                                                         \
-                    qn[nn + __popc(mn & lt)] = make_int2(b, k);                                              \
-            }                                                                                                \
-            nf += __popc(mf);                                                                                \
-            nn += __popc(mn);                                                                                \
-            __syncwarp();                                                                                    \
-            if (nn >= 32) {                                                                                  \
-                nn -= 32;                                                                                    \
-                run(qn, nn, 32, std::false_type{});                                                          \
-            }                                                                                                \
-            if (nf >= 32) {                                                                                  \
-                nf -= 32;                                                                                    \
-                run(qf, nf, 32, std::true_type{});                                                           \
-            }                                                                                                \
-        }                                                                                                    \
-        if (nn > 0) run(qn, 0, nn, std::false_type{});                                                       \
-        if (nf > 0) run(qf, 0, nf, std::true_type{});                                                        \
-        if (a.prim_count) {                                                                                  \
-            const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \
-            if (lane == 0 && w) atomicAdd(a.prim_count, w);                                                  \
-        }                                                                                                    \
-    }                                                                                                        \
-    void launch_eri_fn_##NAME(const EriArgs& a, int grid, int block, cudaStream_t s)                         \
-    {                                                                                                        \
-        k_eri_fn_##NAME<<<grid, block, 0, s>>>(a);                                                           \
     }
 
 // Rys-quadrature variant of a class: the same kernel body around quartet_rys_NAME, FP64 and the ket

@@ -202,7 +202,6 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
 
 
 RYS_MIN_L = 6  # classes evaluated by Rys quadrature when asked for (HF_RYS)
-FARNEAR_MAX_L = 3  # classes whose FP64 launches sort quartets into near and far warps
 
 
 def gen_rys_prim(la, lb, lc, ld, cnt, subset=None):
@@ -316,7 +315,7 @@ def gen_setup(L, used, cnt):
         "const real T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);",
         "const real pref = bK * kp.K * rs;",
         f"real F[{L + 1}];",
-        f"boys<real, {L}, FAR>(T, boys_tab, F);",
+        f"boys<real, {L}>(T, boys_tab, F);",
     ]
     cnt_setup = 1 + 8 + 1 + 3 + 2 + 6 + 2
     if L > 0:
@@ -599,9 +598,8 @@ def gen_class(X, Y, method="os"):
     out.append(f"// Lanes per quartet in the ERI kernels: {G}.  The G lanes of a group share one shell quartet's")
     out.append(f"// primitive staircase round-robin and sum their accumulators with butterfly shuffles; lane 0")
     out.append(f"// then runs the horizontal recurrence and the digestion.  Called warp-uniformly; a lane with")
-    out.append(f"// valid == false takes part in the shuffles only.  FAR: every primitive quartet has T at or past the")
-    out.append(f"// Boys switch point, so only the asymptotic form is evaluated (far/near kernels).")
-    out.append(f"template <typename real, int G, typename KV, bool FAR = false>")
+    out.append(f"// valid == false takes part in the shuffles only.")
+    out.append(f"template <typename real, int G, typename KV>")
     out.append(f"__device__ __forceinline__ int {qname}(const PairHdr& hb, const PairHdr& hk, const KV& kv,"
                f" const PrimPair<real>* __restrict__ prims, const real* __restrict__ boys_tab,")
     out.append(f"    const real* __restrict__ Pd, int N, real fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
@@ -664,8 +662,6 @@ def gen_class(X, Y, method="os"):
     else:
         out.append(f"ERI_BATCH_KERNEL({name}, {G})")
         out.append(f"ERI_CLASS_KERNELS({name}, {X}, {Y}, {G})")
-        if L <= FARNEAR_MAX_L:
-            out.append(f"ERI_FARNEAR_KERNEL({name}, {L})")
         if X == Y:
             out.append(f"SCHWARZ_KERNEL({name})")
     info = dict(name=name, X=X, Y=Y, l=[la, lb, lc, ld], L=L, G=G, prim_flops=prim_flops, cont_flops=cnt.cont,
@@ -714,8 +710,6 @@ def main(outdir):
         if info["rys"]:
             lines.append(f"void launch_eri_rys_{n}(const EriArgs&, int, int, int, cudaStream_t, int);")
             lines.append(f"size_t local_bytes_rys_{n}();")
-        if info["L"] <= FARNEAR_MAX_L:
-            lines.append(f"void launch_eri_fn_{n}(const EriArgs&, int, int, cudaStream_t);")
     lines.append("")
     lines.append("const EriClassEntry kEriClasses[kNumClasses] = {")
     for info in infos:
@@ -723,9 +717,8 @@ def main(outdir):
         lines.append(f"    {{{info['X']}, {info['Y']}, {info['L']}, {info['prim_flops']}, {info['cont_flops']}, "
                      f"launch_eri_{n}, {('launch_schwarz_' + n) if info['X'] == info['Y'] else 'nullptr'}, \"{n}\", "
                      f"launch_eri_batch_{n}, local_bytes_{n}, {info['G']}, "
-                     + (f"launch_eri_rys_{n}, {info['prim_flops_rys']}, local_bytes_rys_{n}, " if info["rys"]
-                        else "nullptr, 0, nullptr, ")
-                     + (f"launch_eri_fn_{n}}}," if info["L"] <= FARNEAR_MAX_L else "nullptr},"))
+                     + (f"launch_eri_rys_{n}, {info['prim_flops_rys']}, local_bytes_rys_{n}}}," if info["rys"]
+                        else "nullptr, 0, nullptr},"))
     lines.append("};")
     lines.append("}  // namespace hf")
     text = "\n".join(lines) + "\n"

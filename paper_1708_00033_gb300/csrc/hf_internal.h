@@ -27,14 +27,6 @@ struct PairHdr {
     float ABfx, ABfy, ABfz;  // A - B in FP32 (the FP32 kernels' horizontal step uses no FP64 instruction)
 };
 
-// Where the primitive-pair centres of a pair lie and how diffuse its primitives are: every centre
-// P = (a A + b B) / (a + b) is within r of (cx, cy, cz), and pmin is the smallest exponent sum a + b.
-// From these, a quartet's smallest Boys argument T = rho |P - Q|^2 is bounded below (far/near split).
-struct PairGeo {
-    float cx, cy, cz, r;
-    float pmin, pad0, pad1, pad2;
-};
-
 struct EriArgs {
     const PairHdr* pairs;
     const void* prims64;  // PrimPair<double>[]
@@ -69,7 +61,6 @@ struct EriArgs {
                                       // FP64 Obara-Saika kernels read each pair's own records
     const float* ktB;                 // primitive-pair bounds of the ket table
     long long kstride;                // kets per field row of the ket table
-    const PairGeo* pgeo;              // [pair id] centre intervals (far/near kernels)
     const PairHdr* bhdr;              // headers of the bra list in list order (bhdr[b] = pairs[bra[b]])
     const PairHdr* khdr;              // headers of the ket list in list order (khdr[k] = pairs[ket[k]])
 };
@@ -126,8 +117,6 @@ struct EriClassEntry {
     void (*launch_rys)(const EriArgs&, int use_f32, int grid, int block, cudaStream_t, int lanes);
     int prim_flops_rys;       // per primitive quartet (setup + roots + 2D recurrences + accumulation)
     size_t (*local_bytes_rys)();
-    // far/near variant (low-L classes; nullptr otherwise): FP64, one lane per quartet, no density screening
-    void (*launch_fn)(const EriArgs&, int grid, int block, cudaStream_t);
 };
 extern const EriClassEntry kEriClasses[kNumClasses];
 
@@ -207,7 +196,7 @@ struct hf_system {
     hf::DevBuf comp_norm;  // [n_bf] Cartesian component factor
     // pairs
     int n_pairs_all = 0, n_prim_pairs = 0;
-    hf::DevBuf pairs, prims64, prims32, pair_class, pair_geo;
+    hf::DevBuf pairs, prims64, prims32, pair_class;
     int class_count[hf::kNumPairClasses] = {};
     hf::DevBuf class_ids[hf::kNumPairClasses];  // sorted significant pair ids
     double Qmax = 0.0;

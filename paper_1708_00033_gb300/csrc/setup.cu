@@ -115,7 +115,7 @@ __global__ void k_build_pairs(long long n_pairs, int maxpp, const int* __restric
                               const double* __restrict__ exps, const double* __restrict__ cn,
                               const double* __restrict__ xyz, PairHdr* __restrict__ pairs,
                               PrimPair<double>* __restrict__ p64, PrimPair<float>* __restrict__ p32,
-                              int* __restrict__ pclass, PairGeo* __restrict__ geo)
+                              int* __restrict__ pclass)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_pairs) return;
@@ -145,27 +145,6 @@ __global__ void k_build_pairs(long long n_pairs, int maxpp, const int* __restric
     pairs[t] = h;
     pclass[t] = la * (la + 1) / 2 + lb;
     const double c52 = sqrt(2.0) * pow(M_PI, 1.25);  // sqrt(2) pi^(5/4)
-    // centre interval: P = A - t AB with t = b / (a + b) over the primitive pairs
-    double tmin = 1.0, tmax = 0.0, pmin = 1e300;
-    for (int ka = 0; ka < nprim[A]; ka++)
-        for (int kb = 0; kb < nprim[B]; kb++) {
-            const double a = exps[prim0[A] + ka], b = exps[prim0[B] + kb];
-            const double tt = b / (a + b);
-            tmin = fmin(tmin, tt);
-            tmax = fmax(tmax, tt);
-            pmin = fmin(pmin, a + b);
-        }
-    {
-        const double tc = 0.5 * (tmin + tmax);
-        PairGeo g;
-        g.cx = (float)(Ax - tc * ABx);
-        g.cy = (float)(Ay - tc * ABy);
-        g.cz = (float)(Az - tc * ABz);
-        g.r = (float)(0.5 * (tmax - tmin) * sqrt(R2));
-        g.pmin = (float)pmin;
-        g.pad0 = g.pad1 = g.pad2 = 0.0f;
-        geo[t] = g;
-    }
     int k = 0;
     for (int ka = 0; ka < nprim[A]; ka++) {
         const double a = exps[prim0[A] + ka], ca = cn[prim0[A] + ka];
@@ -522,12 +501,12 @@ int launch_comp_norm(int n_sh, const int* l, const int* bf0, double* out, cudaSt
 
 int launch_build_pairs(long long n_pairs, int maxpp, const int* l, const int* atom, const int* bf0, const int* nprim,
                        const int* prim0, const double* exps, const double* cn, const double* xyz, PairHdr* pairs,
-                       void* p64, void* p32, int* pclass, PairGeo* geo, cudaStream_t s)
+                       void* p64, void* p32, int* pclass, cudaStream_t s)
 {
     if (n_pairs == 0) return 0;
     k_build_pairs<<<(unsigned)((n_pairs + 127) / 128), 128, 0, s>>>(n_pairs, maxpp, l, atom, bf0, nprim, prim0, exps, cn,
                                                                   xyz, pairs, (PrimPair<double>*)p64,
-                                                                  (PrimPair<float>*)p32, pclass, geo);
+                                                                  (PrimPair<float>*)p32, pclass);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -12,7 +12,7 @@ int launch_shell_coef(int n_sh, const int* l, const int* nprim, const int* prim0
 int launch_comp_norm(int n_sh, const int* l, const int* bf0, double* out, cudaStream_t s);
 int launch_build_pairs(long long n_pairs, int maxpp, const int* l, const int* atom, const int* bf0, const int* nprim,
                        const int* prim0, const double* exps, const double* cn, const double* xyz, PairHdr* pairs,
-                       void* p64, void* p32, int* pclass, PairGeo* geo, cudaStream_t s);
+                       void* p64, void* p32, int* pclass, cudaStream_t s);
 int launch_class_count(long long n, const int* pclass, unsigned long long* cnt, cudaStream_t s);
 int launch_class_scatter_all(long long n, const int* pclass, int X, unsigned* cursor, int* ids, cudaStream_t s);
 int launch_copy_q(long long n, const double* Q, PairHdr* pairs, unsigned long long* qmax_bits, cudaStream_t s);
