@@ -140,6 +140,21 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
         need(t)
     order = sorted(recipe.keys(), key=lambda n: (sum(n[0]) + sum(n[1]), sum(n[1]), -n[2]))
     used = set()
+    # WP_i = -(rho/p) PQ_i and WQ_i = (rho/q) PQ_i cost three multiplies per primitive quartet; when fewer
+    # than three distinct values are multiplied by them, (rho/p) is folded into those values instead
+    # (u = rho_p x, and WP_i x = -PQ_i u), which saves multiplies (the smallest classes only)
+    wp_ops, wq_ops, wp_co, wq_co = set(), set(), set(), set()
+    for node, r in recipe.items():
+        if r[0] == "e1":
+            wp_ops.add(vname(sub(node[0], r[1]), Z3, node[2] + 1))
+            wp_co.add(r[1])
+        elif r[0] == "e2":
+            wq_ops.add(vname(node[0], sub(node[1], r[1]), node[2] + 1))
+            wq_co.add(r[1])
+    fold_p = FOLD and 0 < len(wp_ops) < len(wp_co)
+    fold_q = FOLD and 0 < len(wq_ops) < len(wq_co)
+    # the algorithmic count keeps the WP_i / WQ_i products (the setup counts them when they are formed)
+    cnt.prim += (len(wp_co) if fold_p else 0) + (len(wq_co) if fold_q else 0)
     # targets no other node depends on are accumulated as an FMA chain of their recurrence terms
     # (acc = fma(c_k, x_k, acc) per term) instead of forming their value and adding it
     depended = set()
@@ -148,6 +163,14 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
             depended.update(r[-1])
     tset = set(targets)
     leaf = {n for n in tset if n not in depended and recipe[n][0] != "base"}
+    def fold_lines(nm):
+        out_ = []
+        if fold_p and nm in wp_ops:
+            out_.append(f"const real up_{nm} = rho_p * {nm};")
+        if fold_q and nm in wq_ops:
+            out_.append(f"const real uq_{nm} = rho_q * {nm};")
+        return out_
+
     lines = []
     acc = []
     for node in order:
@@ -156,6 +179,7 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
         nm = vname(e, f, m)
         if r[0] == "base":
             lines.append(f"const real {nm} = pref * F[{m}];")
+            lines += fold_lines(nm)
             cnt.prim += 1
             continue
         i = r[1]
@@ -163,8 +187,12 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
         terms = []  # (coefficient, operand)
         if r[0] == "e1":
             e1 = sub(e, i)
-            terms += [(f"PA{a}", vname(e1, Z3, m)), (f"WP{a}", vname(e1, Z3, m + 1))]
-            used.update({f"PA{a}", f"WP{a}"})
+            if fold_p:
+                terms += [(f"PA{a}", vname(e1, Z3, m)), (f"-PQ{a}", "up_" + vname(e1, Z3, m + 1))]
+                used.update({f"PA{a}", "rho_p"})
+            else:
+                terms += [(f"PA{a}", vname(e1, Z3, m)), (f"WP{a}", vname(e1, Z3, m + 1))]
+                used.update({f"PA{a}", f"WP{a}"})
             cnt.prim += 3
             if e[i] >= 2:
                 e2 = sub(e, i, 2)
@@ -174,8 +202,12 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
                 cnt.prim += 4
         else:
             f1 = sub(f, i)
-            terms += [(f"QC{a}", vname(e, f1, m)), (f"WQ{a}", vname(e, f1, m + 1))]
-            used.update({f"QC{a}", f"WQ{a}"})
+            if fold_q:
+                terms += [(f"QC{a}", vname(e, f1, m)), (f"PQ{a}", "uq_" + vname(e, f1, m + 1))]
+                used.update({f"QC{a}", "rho_q"})
+            else:
+                terms += [(f"QC{a}", vname(e, f1, m)), (f"WQ{a}", vname(e, f1, m + 1))]
+                used.update({f"QC{a}", f"WQ{a}"})
             cnt.prim += 3
             if f[i] >= 2:
                 f2 = sub(f, i, 2)
@@ -194,6 +226,7 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
                 lines.append(f"{an} = fma({c}, {x}, {an});")
         else:
             lines.append(f"const real {nm} = " + " + ".join(f"{c} * {x}" for c, x in terms) + ";")
+        lines += fold_lines(nm)
     for (e, f, m) in targets:
         if (e, f, m) not in leaf:
             acc.append(f"acc{tstr(e)}_{tstr(f)} += {vname(e, f, 0)};")
@@ -202,6 +235,7 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
 
 
 RYS_MIN_L = 6  # classes evaluated by Rys quadrature when asked for (HF_RYS)
+FOLD = True  # fold rho/p (rho/q) into the recurrence values when that saves multiplies
 
 
 def gen_rys_prim(la, lb, lc, ld, cnt, subset=None):
