@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--reference-seconds", type=float, default=150.0,
                     help="oracle time budget of --impl reference over all its steps")
     ap.add_argument("--mode", default="fock",
-                    choices=["fock", "scf", "mixed", "batch", "guess", "copies", "peaks", "shard", "rys"])
+                    choices=["fock", "scf", "mixed", "batch", "guess", "copies", "peaks", "shard", "rys", "case"])
+    ap.add_argument("--case", default="fock", choices=["fock", "scf", "train"], help="workload of --mode case")
     ap.add_argument("--n-train", type=int, default=2000)
     ap.add_argument("--n-eval", type=int, default=32)
     ap.add_argument("--train-steps", type=int, default=4000)
@@ -646,6 +647,38 @@ def run_rys(a):
     print(json.dumps(line), flush=True)
 
 
+def run_case(a):
+    """Small fixed workloads for profiler captures (no timing, no JSON line): --case fock (two builds of the
+    --waters cluster with --fp32-cutoff), scf (two SCF iterations of the --waters cluster), train (20
+    learned-guess training steps of 2,048 random samples)."""
+    import numpy as np
+    import torch
+    from paper_1708_00033_gb300 import hf, inputs
+    ctx = hf.Context(0)
+    if a.case == "fock":
+        geom = inputs.water_cluster(a.waters, a.config_id, 0)
+        s = hf.System(ctx, geom, inputs.synthetic_basis(geom), schwarz_tau=a.tau, prim_tau=a.prim_tau,
+                      fp32_cutoff=a.fp32_cutoff)
+        S, _ = s.one_electron()
+        P = torch.from_numpy(random_density(S, inputs.n_electrons(geom) // 2, a.config_id, 0)).cuda()
+        for _ in range(2):
+            out = s.fock_build(P, stats=True)
+        torch.cuda.synchronize()
+        print("quartets", out["stats"]["quartets_fp64"], out["stats"]["quartets_fp32"], file=sys.stderr)
+    elif a.case == "scf":
+        geom = inputs.water_cluster(a.waters, a.config_id, 0)
+        s = hf.System(ctx, geom, inputs.synthetic_basis(geom), schwarz_tau=a.tau, prim_tau=a.prim_tau)
+        r = hf.scf(s, max_iter=2, raise_on_noconv=False)
+        print("scf", r["iterations"], r["energy"], file=sys.stderr)
+    else:
+        rng = np.random.default_rng(0)
+        X = torch.from_numpy(rng.standard_normal((4096, 16)).astype(np.float32)).cuda()
+        T = torch.from_numpy(rng.standard_normal((4096, 325)).astype(np.float32)).cuda()
+        m = hf.Model(ctx, inputs.guess_init_weights(0))
+        hf.guess_train(m, X, T, torch.ones_like(T), steps=20, batch=2048)
+        print("train done", file=sys.stderr)
+
+
 def _scf_run(hf, sysm, **kw):
     import torch
     torch.cuda.synchronize()
@@ -915,6 +948,8 @@ def main():
         run_shard(a)
     elif a.mode == "rys":
         run_rys(a)
+    elif a.mode == "case":
+        run_case(a)
     else:
         run_ours(a)
 
