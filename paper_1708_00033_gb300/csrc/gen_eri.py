@@ -236,7 +236,6 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
 
 RYS_MIN_L = 6  # classes evaluated by Rys quadrature when asked for (HF_RYS)
 FOLD = True  # fold rho/p (rho/q) into the recurrence values when that saves multiplies
-PREFETCH_MAX_P = 32  # classes whose six density blocks hold at most this many elements prefetch them (FP32)
 
 
 def gen_rys_prim(la, lb, lc, ld, cnt, subset=None):
@@ -556,8 +555,6 @@ def gen_class(X, Y, method="os"):
     cont_hrr = cnt.cont
     dig = gen_digest(la, lb, lc, ld, xname, cnt)
     prim_flops = cnt.prim + cset + extra
-    ploads = [l for l in dig if l.startswith("const real P")]
-    prefetch = len(ploads) <= PREFETCH_MAX_P
     tnames = [f"acc{tstr(e)}_{tstr(f)}" for (e, f, m) in targets]
     need_ab = any("AB" in l for l in hrr)
     need_cd = any("CD" in l for l in hrr)
@@ -659,14 +656,6 @@ def gen_class(X, Y, method="os"):
     out.append("        while (nkb0 > 0 && bpp[0].B * kv.B(nkb0 - 1) < ptau) nkb0--;")
     out.append("    }")
     out.append("    int nq = 0;")
-    if prefetch:
-        out.append("    // FP32 launches load the density blocks of the digestion before the primitive loop, so that")
-        out.append("    // their latency overlaps the loop (FP64 launches, bound by the FP64 pipe, load them after it)")
-        out.append("    const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
-        out.append("    real " + ", ".join(l.split(" = ")[0].split()[-1] for l in ploads) + ";")
-        out.append("    if constexpr (sizeof(real) == 4) {")
-        out += ["        " + l.replace("const real ", "") for l in ploads]
-        out.append("    }")
     if not chunked:
         p_ = pass_lines(targets, True, False)
         # single pass: its accumulators stay in scope for the horizontal step
@@ -695,16 +684,9 @@ def gen_class(X, Y, method="os"):
     tail.append("    return;")
     tail.append("}")
     tail.append("if (total == 0) return;  // every primitive quartet screened: nothing to digest")
-    if not prefetch:
-        tail.append("const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
+    tail.append("const int bA = hb.bfA, bB = hb.bfB, bC = hk.bfA, bD = hk.bfB;")
     tail.append("const real fj = real(4) * fscale, fk = real(2) * fscale;")
-    if prefetch:
-        tail.append("if constexpr (sizeof(real) == 8) {")
-        tail += ["    " + l.replace("const real ", "") for l in ploads]
-        tail.append("}")
-        tail += [l for l in dig if l not in ploads]
-    else:
-        tail += dig
+    tail += dig
     out += ["    " + l.replace("return;", "return nq;") for l in tail]
     out.append("    return nq;")
     out.append("}")
