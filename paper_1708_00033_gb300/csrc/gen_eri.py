@@ -583,39 +583,63 @@ def gen_class(X, Y, method="os"):
         lines += list(acc_of.values())
         return lines
 
-    def pass_lines(chunk, first, store):
-        """One pass over the primitive staircase accumulating `chunk`."""
+    def loop_lines(chunk, first, order):
+        """The loop over the primitive staircase for `chunk`: order "bra" (bra-major, the FP64 kernels) or
+        "ket" (ket-major, the FP32 kernels: a lane reloads its ket record only when its ket primitive
+        changes, which removes most of the ket loads that bound them on L1)."""
+        o = ["// lane l evaluates staircase positions l, l + G, l + 2G, ... in lockstep with its group"]
+        if order == "bra":
+            o += ["int nkb = nkb0, ib = 0, ik = 0;",
+                  "auto advance = [&]() {",
+                  "    if (++ik == nkb) {",
+                  "        ik = 0;",
+                  "        ib++;",
+                  "        if (ib < nbp)",
+                  "            while (nkb > 0 && bpp[ib].B * kv.B(nkb - 1) < ptau) nkb--;",
+                  "    }",
+                  "};"]
+        else:
+            o += ["int nbb = nbb0, ib = 0, ik = 0, lk = -1;",
+                  "PrimPair<real> kp;",
+                  "auto advance = [&]() {",
+                  "    if (++ib == nbb) {",
+                  "        ib = 0;",
+                  "        ik++;",
+                  "        if (ik < nkp)",
+                  "            while (nbb > 0 && bpp[nbb - 1].B * kv.B(ik) < ptau) nbb--;",
+                  "    }",
+                  "};"]
+        o += ["if (G > 1)",
+              "    for (int s = 0; s < lane && s < total; s++) advance();",
+              "for (int it = (G > 1 ? lane : 0); it < total; it += G) {",
+              "    const int cib = ib, cik = ik;",
+              "#pragma unroll",
+              "    for (int s = 0; s < G; s++) advance();"]
+        if first:
+            o.append("    nq++;")
+        o.append("    const PrimPair<real> bp = bpp[cib];")
+        if order == "bra":
+            o.append("    const PrimPair<real> kp = kv.rec(cik);")
+        else:
+            o += ["    if (cik != lk) {", "        kp = kv.rec(cik);", "        lk = cik;", "    }"]
+        o += ["    " + l for l in prim_body(chunk)]
+        o.append("}")
+        return o
+
+    def shuffle_lines(chunk):
+        cn = [f"acc{tstr(e)}_{tstr(f)}" for (e, f, m) in chunk]
+        o = ["if constexpr (G > 1) {", "#pragma unroll", "    for (int o = 1; o < G; o <<= 1) {"]
+        o += [f"        {nm} += __shfl_xor_sync(0xffffffffu, {nm}, o);" for nm in cn]
+        o += ["    }", "}"]
+        return o
+
+    def pass_lines(chunk, first, store, order):
+        """One pass over the primitive staircase accumulating `chunk` (its own scope)."""
         cn = [f"acc{tstr(e)}_{tstr(f)}" for (e, f, m) in chunk]
         o = ["{"]
         o += [f"    real {nm} = real(0);" for nm in cn]
-        o.append("    // lane l evaluates staircase positions l, l + G, l + 2G, ... in lockstep with its group")
-        o.append("    int nkb = nkb0, ib = 0, ik = 0;")
-        o.append("    auto advance = [&]() {")
-        o.append("        if (++ik == nkb) {")
-        o.append("            ik = 0;")
-        o.append("            ib++;")
-        o.append("            if (ib < nbp)")
-        o.append("                while (nkb > 0 && bpp[ib].B * kv.B(nkb - 1) < ptau) nkb--;")
-        o.append("        }")
-        o.append("    };")
-        o.append("    if (G > 1)")
-        o.append("        for (int s = 0; s < lane && s < total; s++) advance();")
-        o.append("    for (int it = (G > 1 ? lane : 0); it < total; it += G) {")
-        o.append("        const int cib = ib, cik = ik;")
-        o.append("#pragma unroll")
-        o.append("        for (int s = 0; s < G; s++) advance();")
-        if first:
-            o.append("        nq++;")
-        o.append("        const PrimPair<real> bp = bpp[cib];")
-        o.append("        const PrimPair<real> kp = kv.rec(cik);")
-        o += ["        " + l for l in prim_body(chunk)]
-        o.append("    }")
-        o.append("    if constexpr (G > 1) {")
-        o.append("#pragma unroll")
-        o.append("        for (int o = 1; o < G; o <<= 1) {")
-        o += [f"            {nm} += __shfl_xor_sync(0xffffffffu, {nm}, o);" for nm in cn]
-        o.append("        }")
-        o.append("    }")
+        o += ["    " + l for l in loop_lines(chunk, first, order)]
+        o += ["    " + l for l in shuffle_lines(chunk)]
         if store:
             o += [f"    accv[{tnames.index(nm)}] = {nm};" for nm in cn]
         o.append("}")
@@ -639,12 +663,13 @@ def gen_class(X, Y, method="os"):
     out.append(f"    const real* __restrict__ Pd, int N, real fscale, double* __restrict__ Jt, double* __restrict__ Kt, double* qout,")
     out.append(f"    float ptau, int lane, bool valid)")
     out.append("{")
-    out.append("    // surviving primitive quartets form a staircase (pairs sorted by bound): bra primitive ib")
-    out.append("    // pairs with the first nk(ib) ket primitives, nk non-increasing; one flat loop over it.")
+    out.append("    // surviving primitive quartets form a staircase (pairs sorted by bound): bra primitive ib pairs")
+    out.append("    // with the first nk(ib) ket primitives, nk non-increasing (equivalently ket primitive ik with the")
+    out.append("    // first nb(ik) bra primitives); one flat loop over it, bra-major in FP64, ket-major in FP32.")
     out.append("    // kv: the ket's records (KetAos: the pair's record array; KetSoa: its column of the class's ket table)")
     out.append("    const PrimPair<real>* __restrict__ bpp = prims + hb.prim0;")
-    out.append("    const int nbp = hb.nprim;")
-    out.append("    int nkb0 = hk.nprim;")
+    out.append("    const int nbp = hb.nprim, nkp = hk.nprim;")
+    out.append("    int nkb0 = nkp, nbb0 = nbp;")
     out.append("    int total = 0;")
     out.append("    if (valid) {")
     out.append("        for (int ib = 0, c = nkb0; ib < nbp; ib++) {")
@@ -654,18 +679,24 @@ def gen_class(X, Y, method="os"):
     out.append("            total += c;")
     out.append("        }")
     out.append("        while (nkb0 > 0 && bpp[0].B * kv.B(nkb0 - 1) < ptau) nkb0--;")
+    out.append("        while (nbb0 > 0 && bpp[nbb0 - 1].B * kv.B(0) < ptau) nbb0--;")
     out.append("    }")
     out.append("    int nq = 0;")
     if not chunked:
-        p_ = pass_lines(targets, True, False)
-        # single pass: its accumulators stay in scope for the horizontal step
-        out += ["    " + l for l in p_[1:-1]]
+        # single pass: the accumulators stay in scope for the horizontal step
+        out += [f"    real {nm} = real(0);" for nm in tnames]
+        out.append("    if constexpr (sizeof(real) == 8) {")
+        out += ["        " + l for l in loop_lines(targets, True, "bra")]
+        out.append("    } else {")
+        out += ["        " + l for l in loop_lines(targets, True, "ket")]
+        out.append("    }")
+        out += ["    " + l for l in shuffle_lines(targets)]
     else:
         out.append(f"    real accv[{len(targets)}];  // finished chunks of targets")
         for sz, kw in ((8, "if constexpr (sizeof(real) == 8)"), (4, "else")):
             out.append(f"    {kw} {{")
             for k, c in enumerate(ch[sz]):
-                out += ["        " + l for l in pass_lines(c, k == 0, True)]
+                out += ["        " + l for l in pass_lines(c, k == 0, True, "bra" if sz == 8 else "ket")]
             out.append("    }")
         out += [f"    const real {nm} = accv[{i}];" for i, nm in enumerate(tnames)]
     out.append("    if (!valid || lane != 0) return nq;")
