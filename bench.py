@@ -610,7 +610,8 @@ def run_shard(a):
 
 def run_rys(a):
     """Rys quadrature vs Obara-Saika for the classes of total angular momentum L >= 6: per-class device time
-    of the same FP64 Fock build (best of `steps` after `warmup`), with the largest difference of F."""
+    of the same FP64 Fock build (best of `steps` after `warmup`), with the largest difference of F; and the
+    build with the library's per-class default choice."""
     import numpy as np
     import torch
     from paper_1708_00033_gb300 import hf, inputs
@@ -621,7 +622,7 @@ def run_rys(a):
     S, _ = s.one_electron()
     Pd = torch.from_numpy(random_density(S, inputs.n_electrons(geom) // 2, a.config_id, 0)).cuda()
     res = {}
-    for name, rys in (("obara_saika", False), ("rys", True)):
+    for name, rys in (("obara_saika", False), ("rys", True), ("default", None)):
         F = torch.empty_like(Pd)
         for _ in range(max(1, a.warmup)):
             s.fock_build(Pd, F=F, rys=rys)
@@ -646,7 +647,9 @@ def run_rys(a):
             "dtype": "f64", "data": "synthetic", "config": {"workload": workload_name(a)},
             "classes": rows, "total_ms_os": tot_os, "total_ms_rys": tot_rys, "speedup_rys": tot_os / tot_rys,
             "build_ms_os": res["obara_saika"]["stats"]["ms_total"], "build_ms_rys": res["rys"]["stats"]["ms_total"],
-            "max_abs_dF": float((res["rys"]["F"] - res["obara_saika"]["F"]).abs().max())}
+            "build_ms_default": res["default"]["stats"]["ms_total"],
+            "max_abs_dF": float((res["rys"]["F"] - res["obara_saika"]["F"]).abs().max()),
+            "max_abs_dF_default": float((res["default"]["F"] - res["obara_saika"]["F"]).abs().max())}
     print(json.dumps(line), flush=True)
 
 

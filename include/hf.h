@@ -55,11 +55,16 @@ extern "C" {
 #define HF_FP64_ONLY 8  /* hf_fock_build: evaluate the FP32 part of a mixed system in FP64 too */
 #define HF_DENSITY_SCREEN 16 /* hf_fock_build_partial: also skip quartets whose Schwarz bound times the
                                 largest |P| of the six density blocks they touch (x4) is below schwarz_tau */
-#define HF_RYS 32            /* hf_fock_build, hf_fock_build_partial: evaluate the FP64 quartets of the classes
-                                of total angular momentum L >= 6 ((dp|dp), (dd|pp), (dd|ds), (dd|dp),
+#define HF_RYS 32            /* hf_fock_build, hf_fock_build_partial: evaluate the FP64 quartets of all five
+                                classes of total angular momentum L >= 6 ((dp|dp), (dd|pp), (dd|ds), (dd|dp),
                                 (dd|dd)) by Rys quadrature (L/2 + 1 nodes of the Boys weight) instead of the
                                 Obara-Saika vertical recurrence; the contraction, horizontal recurrence and
-                                digestion are shared, so results agree to rounding */
+                                digestion are shared, so results agree to rounding.  Without HF_RYS or
+                                HF_OBARA_SAIKA the builds use Rys for the four of them where it is faster
+                                ((dp|dp), (dd|ds), (dd|dp), (dd|dd)) and Obara-Saika for (dd|pp).  FP32
+                                launches and the batched builds always use Obara-Saika. */
+#define HF_OBARA_SAIKA 64    /* hf_fock_build, hf_fock_build_partial: Obara-Saika for every class (no Rys);
+                                with HF_RYS as well, HF_OBARA_SAIKA wins */
 
 typedef struct hf_ctx hf_ctx;       /* one device + one stream + constant tables */
 typedef struct hf_system hf_system; /* one molecule: basis, pairs, screening plan, 1e matrices */

@@ -143,8 +143,8 @@ int hf_create(hf_ctx** out, int device, void* cuda_stream)
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     c->num_sms = prop.multiProcessorCount;
-    int rc = c->boys64.alloc(sizeof(double) * kBoysRows * kBoysStride64);
-    if (rc == HF_OK) rc = c->boys32.alloc(sizeof(float) * kBoysRows * kBoysStride32);
+    int rc = c->boys64.alloc(sizeof(double) * kBoysRows64 * kBoysStride64);
+    if (rc == HF_OK) rc = c->boys32.alloc(sizeof(float) * kBoysRows32 * kBoysStride32);
     if (rc == HF_OK && build_boys_tables(c->boys64.as<double>(), c->boys32.as<float>(), c->stream) != 0)
         rc = cuda_status(cudaGetLastError(), "boys table kernel");
     if (rc == HF_OK) {
@@ -696,11 +696,11 @@ int hf_system_set_fock_copies(hf_system* S, int32_t copies)
 
 }  // extern "C"
 
-// Whether a launch of class ci runs the Rys-quadrature kernel: asked for (HF_RYS), an FP64 launch, a class
-// that has one, and the ket tables in use.
+// Whether a launch of class ci runs the Rys-quadrature kernel: an FP64 launch of a class whose Rys variant
+// the flags select (class_uses_rys), with the ket tables in use.
 static bool uses_rys(int ci, int flags, int use_f32, const EriArgs& a)
 {
-    return (flags & HF_RYS) && !use_f32 && kEriClasses[ci].launch_rys && a.kt;
+    return !use_f32 && class_uses_rys(ci, flags) && a.kt;
 }
 // (the ket tables always exist for a class with significant pairs, so a.kt is set for every launch)
 
@@ -841,7 +841,7 @@ int hf_fock_build(hf_system* S, const double* P, double* F, double* J, double* K
             stats->prim_quartets_fp64 += (int64_t)pc[2 * ci];
             stats->prim_quartets_fp32 += (int64_t)pc[2 * ci + 1];
             const double pf = kEriClasses[ci].prim_flops, cf = kEriClasses[ci].cont_flops;
-            const bool rys = (flags & HF_RYS) && kEriClasses[ci].launch_rys;
+            const bool rys = class_uses_rys(ci, flags);
             const double pf64 = rys ? kEriClasses[ci].prim_flops_rys : pf;
             const double pf32 = (rys && (flags & HF_FP64_ONLY)) ? pf64 : pf;  // FP32 launches stay Obara-Saika
             stats->class_flops_fp64[ci] = pf64 * (double)pc[2 * ci] + cf * (double)pl.n64;

@@ -62,16 +62,20 @@ struct KetSoa {
     __device__ __forceinline__ float B(int i) const { return __ldg(fB + (long long)i * stride); }
 };
 
-// Boys tables, rows T_k = k / 32 for k = 0..kBoysRows-1 (T < 60), stored in
-// Taylor-coefficient form so that evaluation is a pure Horner chain:
-//   FP64 row: c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..6) at m*7 + j,
-//             e^{-T_k} / j! (j = 0..7) at 63 + j;
-//   FP32 row: c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..3) at m*4 + j,
+// Boys tables in Taylor-coefficient form, so that evaluation is a pure Horner chain (T < 60):
+//   FP64 rows T_k = k / 512, k = 0..kBoysRows64-1:
+//             c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..4) at m*5 + j,
+//             e^{-T_k} / j! (j = 0..4) at 45 + j;
+//   FP32 rows T_k = k / 32, k = 0..kBoysRows32-1:
+//             c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..3) at m*4 + j,
 //             e^{-T_k} / j! (j = 0..4) at 36 + j.
-constexpr int kBoysRows = 1921;
-constexpr int kBoysStride64 = 72;
+// The FP64 grid is fine so that each FP64 Horner chain is short: FP64 instructions are the scarce
+// resource of the ERI kernels, table loads are not.
+constexpr int kBoysRows64 = 60 * 512 + 1;
+constexpr int kBoysRows32 = 60 * 32 + 1;
+constexpr int kBoysStride64 = 50;
 constexpr int kBoysStride32 = 44;
-constexpr int kBoysExp64 = 63;
+constexpr int kBoysExp64 = 45;
 constexpr int kBoysExp32 = 36;
 constexpr double kBoysTmax = 60.0;
 
@@ -94,31 +98,32 @@ __host__ __device__ constexpr float boys_switch32(int L)
 }
 
 // F_m(T), m = 0..L.  Below boys_switch64(L) (<= 59, inside the tables' T < 60): Taylor expansion about the
-// nearest grid point T_k (|T - T_k| <= 1/64; seven terms, truncation < 5e-17 relative), using
-// dF_m/dT = -F_{m+1}; for L >= 2 only F_L is expanded and the rest follow from the downward recursion
-// F_m = (2T F_{m+1} + e^{-T}) / (2m+1), with e^{-T} = e^{-T_k} e^{T_k - T} expanded the same way.  Above:
-// F_0 = sqrt(pi/T)/2 and the upward recursion F_{m+1} = (2m+1) F_m / (2T) (the e^{-T} terms dropped).
-// The grid index is the integer that T*32 + 1.5*2^52 rounds to, read from the low word of the sum.
+// nearest grid point T_k (|T - T_k| <= 1/1024; five terms, truncation below (1/1024)^5 / 5! < 1e-17
+// relative, as |F_{m+5}| <= |F_m|), using dF_m/dT = -F_{m+1}; for L >= 2 only F_L is expanded and the rest
+// follow from the downward recursion F_m = (2T F_{m+1} + e^{-T}) / (2m+1), with e^{-T} = e^{-T_k} e^{T_k - T}
+// expanded the same way.  Above: F_0 = sqrt(pi/T)/2 and the upward recursion F_{m+1} = (2m+1) F_m / (2T)
+// (the e^{-T} terms dropped).  The grid index is the integer that T*512 + 1.5*2^52 rounds to, read from the
+// low word of the sum.
 template <int L>
 __device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double* F)
 {
     if (T < boys_switch64(L)) {
         const double big = 6755399441055744.0;  // 1.5 * 2^52
-        const double t = fma(T, 32.0, big);
+        const double t = fma(T, 512.0, big);
         const int k = __double2loint(t);
-        const double d = fma(t - big, 1.0 / 32.0, -T);  // T_k - T
+        const double d = fma(t - big, 1.0 / 512.0, -T);  // T_k - T
         const double* __restrict__ r = tab + k * kBoysStride64;
         if constexpr (L <= 1) {
 #pragma unroll
             for (int m = 0; m <= L; m++) {
-                const double* c = r + 7 * m;
-                F[m] = c[0] + d * (c[1] + d * (c[2] + d * (c[3] + d * (c[4] + d * (c[5] + d * c[6])))));
+                const double* c = r + 5 * m;
+                F[m] = c[0] + d * (c[1] + d * (c[2] + d * (c[3] + d * c[4])));
             }
         } else {
-            const double* c = r + 7 * L;
-            F[L] = c[0] + d * (c[1] + d * (c[2] + d * (c[3] + d * (c[4] + d * (c[5] + d * c[6])))));
+            const double* c = r + 5 * L;
+            F[L] = c[0] + d * (c[1] + d * (c[2] + d * (c[3] + d * c[4])));
             const double* x = r + kBoysExp64;
-            const double e = x[0] + d * (x[1] + d * (x[2] + d * (x[3] + d * (x[4] + d * (x[5] + d * (x[6] + d * x[7]))))));
+            const double e = x[0] + d * (x[1] + d * (x[2] + d * (x[3] + d * x[4])));
             const double t2 = T + T;
 #pragma unroll
             for (int m = L - 1; m >= 0; m--) F[m] = (t2 * F[m + 1] + e) * (1.0 / (2 * m + 1));

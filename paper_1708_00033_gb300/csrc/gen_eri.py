@@ -234,7 +234,10 @@ def gen_vrr(la, lb, lc, ld, cnt, subset=None):
     return lines, acc, used, targets
 
 
-RYS_MIN_L = 6  # classes evaluated by Rys quadrature when asked for (HF_RYS)
+RYS_MIN_L = 6  # classes that have a Rys-quadrature variant (all of them with HF_RYS)
+# Classes whose FP64 launches use the Rys variant by default (neither HF_RYS nor HF_OBARA_SAIKA given): those
+# where it measured faster than the Obara-Saika kernel on the 64-water build ((dd|pp) measured slower).
+RYS_DEFAULT = {"2121", "2220", "2221", "2222"}
 FOLD = True  # fold rho/p (rho/q) into the recurrence values when that saves multiplies
 
 
@@ -276,10 +279,10 @@ def gen_rys_prim(la, lb, lc, ld, cnt, subset=None):
         "const real rs = rsq(s);",
         "const real inv = rs * rs;",
         "const real PQx = bp.Px - kp.Px, PQy = bp.Py - kp.Py, PQz = bp.Pz - kp.Pz;",
-        "const real rho = bp.p * kp.p * inv;",
+        "const real rho_p = kp.p * inv, rho_q = bp.p * inv, o2pq_1 = real(0.5) * inv, ko2p = kp.oo2p;",
+        "const real rho = bp.p * rho_p;",
         "const real T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);",
         "const real pref = bK * kp.K * rs;",
-        "const real rho_p = kp.p * inv, rho_q = bp.p * inv, o2pq_1 = real(0.5) * inv, ko2p = kp.oo2p;",
         "const real QCx = kp.PAx, QCy = kp.PAy, QCz = kp.PAz;",
         f"real ru[{n}], rw[{n}];",
         f"rys_rule<{n}>(T, ru, rw);",
@@ -340,12 +343,18 @@ def gen_rys_prim(la, lb, lc, ld, cnt, subset=None):
 
 def gen_setup(L, used, cnt):
     """Per-primitive-quartet quantities; returns lines (flop counts approximate the emitted ops)."""
+    # rho = p q / (p + q) is formed as p (q / (p + q)) from rho_p where the recurrence needs rho_p anyway:
+    # one FP64 multiply fewer per primitive quartet (the flop count keeps the two of the definition)
     lines = [
         "const real s = bp.p + kp.p;",
         "const real rs = rsq(s);",
         "const real inv = rs * rs;",
         "const real PQx = bp.Px - kp.Px, PQy = bp.Py - kp.Py, PQz = bp.Pz - kp.Pz;",
-        "const real rho = bp.p * kp.p * inv;",
+        "const real rho_p = kp.p * inv;" if L > 0 else "const real rho = bp.p * kp.p * inv;",
+    ]
+    if L > 0:
+        lines += ["const real rho = bp.p * rho_p;"]
+    lines += [
         "const real T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);",
         "const real pref = bK * kp.K * rs;",
         f"real F[{L + 1}];",
@@ -353,7 +362,7 @@ def gen_setup(L, used, cnt):
     ]
     cnt_setup = 1 + 8 + 1 + 3 + 2 + 6 + 2
     if L > 0:
-        lines += ["const real rho_p = kp.p * inv;", "const real rho_q = bp.p * inv;"]
+        lines += ["const real rho_q = bp.p * inv;"]
         cnt_setup += 2
         for a in AX:
             if f"WP{a}" in used:
@@ -782,8 +791,9 @@ def main(outdir):
         lines.append(f"    {{{info['X']}, {info['Y']}, {info['L']}, {info['prim_flops']}, {info['cont_flops']}, "
                      f"launch_eri_{n}, {('launch_schwarz_' + n) if info['X'] == info['Y'] else 'nullptr'}, \"{n}\", "
                      f"launch_eri_batch_{n}, local_bytes_{n}, {info['G']}, "
-                     + (f"launch_eri_rys_{n}, {info['prim_flops_rys']}, local_bytes_rys_{n}}}," if info["rys"]
-                        else "nullptr, 0, nullptr},"))
+                     + (f"launch_eri_rys_{n}, {info['prim_flops_rys']}, local_bytes_rys_{n}, "
+                        f"{1 if n in RYS_DEFAULT else 0}}}," if info["rys"]
+                        else "nullptr, 0, nullptr, 0},"))
     lines.append("};")
     lines.append("}  // namespace hf")
     text = "\n".join(lines) + "\n"

@@ -117,8 +117,17 @@ struct EriClassEntry {
     void (*launch_rys)(const EriArgs&, int use_f32, int grid, int block, cudaStream_t, int lanes);
     int prim_flops_rys;       // per primitive quartet (setup + roots + 2D recurrences + accumulation)
     size_t (*local_bytes_rys)();
+    int rys_default;          // 1: FP64 launches use the Rys variant unless HF_OBARA_SAIKA is given
 };
 extern const EriClassEntry kEriClasses[kNumClasses];
+
+// Whether the FP64 launches of class ci take the Rys variant under these build flags: HF_RYS for every
+// class that has one, HF_OBARA_SAIKA for none, else the class's default.
+inline bool class_uses_rys(int ci, int flags)
+{
+    if (!kEriClasses[ci].launch_rys || (flags & HF_OBARA_SAIKA)) return false;
+    return (flags & HF_RYS) || kEriClasses[ci].rys_default;
+}
 
 // Launches the ERI class kernels of one build: for every class and precision, the quartets
 // [n shard / n_shards, n (shard + 1) / n_shards) of its n screened quartets (shard 0 of 1 is the

@@ -11,16 +11,13 @@
 namespace hf {
 
 // ------------------------------------------------------------ Boys table --
-// F_m(T_k), m = 0..14, at T_k = k/32: the series
+// F_m(T_k), m = 0..14, at the grid points T_k = k/512 (FP64 table) and k/32 (FP32 table): the series
 //   F_M(T) = exp(-T) sum_i (2T)^i / ((2M+1)(2M+3)...(2M+2i+1))
 // for the top order (compensated summation of its positive terms), then the
 // downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1); stored as the
-// Taylor coefficients F_{m+j}(T_k) / j! and exp(-T_k) / j! (see eri_common.cuh).
-__global__ void k_boys_table(double* t64, float* t32)
+// Taylor coefficients F_{m+j}(T_k) / j! and exp(-T_k) / j! (layout in eri_common.cuh).
+__device__ static void boys_row(double T, double* F, double& e)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= kBoysRows) return;
-    const double T = k / 32.0;
     const int M = 14;
     double term = 1.0 / (2 * M + 1), sum = term, comp = 0.0;
     for (int i = 1; i < 1000; i++) {
@@ -31,29 +28,42 @@ __global__ void k_boys_table(double* t64, float* t32)
         sum = t;
         if (term < 1e-21 * sum) break;
     }
-    const double e = exp(-T);
-    double F[M + 1];
+    e = exp(-T);
     F[M] = e * sum;
     for (int m = M - 1; m >= 0; m--) F[m] = (2.0 * T * F[m + 1] + e) / (2 * m + 1);
-    double* r = t64 + (size_t)k * kBoysStride64;
-    float* q = t32 + (size_t)k * kBoysStride32;
-    for (int i = 0; i < kBoysStride64; i++) r[i] = 0.0;
-    for (int i = 0; i < kBoysStride32; i++) q[i] = 0.0f;
-    double fact = 1.0;
-    for (int j = 0; j <= 7; j++) {
-        if (j > 0) fact *= j;
-        for (int m = 0; m <= 8; m++) {
-            if (j <= 6) r[7 * m + j] = F[m + j] / fact;
-            if (j <= 3) q[4 * m + j] = (float)(F[m + j] / fact);
+}
+
+__global__ void k_boys_table(double* t64, float* t32)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double F[15], e;
+    if (k < kBoysRows64) {
+        boys_row(k / 512.0, F, e);
+        double* r = t64 + (size_t)k * kBoysStride64;
+        double fact = 1.0;
+        for (int j = 0; j <= 4; j++) {
+            if (j > 0) fact *= j;
+            for (int m = 0; m <= 8; m++) r[5 * m + j] = F[m + j] / fact;
+            r[kBoysExp64 + j] = e / fact;
         }
-        r[kBoysExp64 + j] = e / fact;
-        if (j <= 4) q[kBoysExp32 + j] = (float)(e / fact);
+    }
+    if (k < kBoysRows32) {
+        boys_row(k / 32.0, F, e);
+        float* q = t32 + (size_t)k * kBoysStride32;
+        for (int i = 0; i < kBoysStride32; i++) q[i] = 0.0f;
+        double fact = 1.0;
+        for (int j = 0; j <= 4; j++) {
+            if (j > 0) fact *= j;
+            if (j <= 3)
+                for (int m = 0; m <= 8; m++) q[4 * m + j] = (float)(F[m + j] / fact);
+            q[kBoysExp32 + j] = (float)(e / fact);
+        }
     }
 }
 
 int build_boys_tables(double* t64, float* t32, cudaStream_t s)
 {
-    k_boys_table<<<(kBoysRows + 127) / 128, 128, 0, s>>>(t64, t32);
+    k_boys_table<<<(kBoysRows64 + 127) / 128, 128, 0, s>>>(t64, t32);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -31,6 +31,7 @@ HF_TIMING = 2
 HF_FP64_ONLY = 8
 HF_DENSITY_SCREEN = 16
 HF_RYS = 32
+HF_OBARA_SAIKA = 64
 NUM_CLASSES = 21
 
 CLASS_NAMES = []
@@ -298,15 +299,16 @@ class System:
         return S, H
 
     def fock_build(self, P, F=None, J=None, K=None, want_J=False, want_K=False, energy=True, stats=False,
-                   timing=False, rys=False, fp64_only=False):
+                   timing=False, rys=None, fp64_only=False):
         """hf_fock_build.  ``P`` may be a numpy array (host path: copies in the
         timed call) or a CUDA float64 tensor (device path).  Output buffers may
-        be passed to avoid allocation.  rys: Rys quadrature for the L >= 6
-        classes (HF_RYS).  Returns a dict with F, J, K, E_elec and optionally
-        stats."""
+        be passed to avoid allocation.  rys: True for Rys quadrature in all five
+        L >= 6 classes (HF_RYS), False for Obara-Saika in every class
+        (HF_OBARA_SAIKA), None for the per-class default.  Returns a dict with
+        F, J, K, E_elec and optionally stats."""
         N = self.n_bf
         lib = load_library()
-        flags = (HF_TIMING if timing else 0) | (HF_RYS if rys else 0) | (HF_FP64_ONLY if fp64_only else 0)
+        flags = (HF_TIMING if timing else 0) | _method_flags(rys) | (HF_FP64_ONLY if fp64_only else 0)
         is_dev = hasattr(P, "is_cuda") and P.is_cuda
         if is_dev:
             torch = _torch()
@@ -533,13 +535,18 @@ def _is_dev(x) -> bool:
     return hasattr(x, "is_cuda") and x.is_cuda
 
 
+def _method_flags(rys) -> int:
+    """ERI method flags: True -> HF_RYS, False -> HF_OBARA_SAIKA, None -> 0 (the per-class default)."""
+    return 0 if rys is None else (HF_RYS if rys else HF_OBARA_SAIKA)
+
+
 def fock_build_partial(system: "System", P, shard: int = 0, n_shards: int = 1, density_screen: bool = False,
-                       fp64_only: bool = False, J=None, K=None, rys: bool = False):
+                       fp64_only: bool = False, J=None, K=None, rys=None):
     """hf_fock_build_partial: (J_shard, K_shard).  ``P`` is a numpy array (host path) or a contiguous float64
     CUDA tensor (device path, outputs are CUDA tensors).  density_screen also skips quartets whose Schwarz
     bound times the largest |P| of the six blocks they touch is below the Schwarz threshold."""
     N = system.n_bf
-    flags = (HF_DENSITY_SCREEN if density_screen else 0) | (HF_FP64_ONLY if fp64_only else 0) | (HF_RYS if rys else 0)
+    flags = (HF_DENSITY_SCREEN if density_screen else 0) | (HF_FP64_ONLY if fp64_only else 0) | _method_flags(rys)
     if _is_dev(P):
         torch = _torch()
         if P.dtype != torch.float64 or not P.is_contiguous() or tuple(P.shape) != (N, N):

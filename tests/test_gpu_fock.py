@@ -335,10 +335,12 @@ def test_sp_shell_basis_scf_vs_oracle(ctx, oracle_mod):
 
 
 def test_rys_quadrature_classes(ctx, oracle_mod):
-    """HF_RYS evaluates the five classes of total angular momentum L >= 6 by Rys quadrature (4 or 5 nodes of
-    the Boys weight) instead of the Obara-Saika vertical recurrence: against the oracle's unscreened J and K
-    (McMurchie-Davidson) at 4 waters within 1e-10, and against the Obara-Saika build to rounding; then with
-    Schwarz and primitive screening at 8 waters against the Obara-Saika build."""
+    """The five classes of total angular momentum L >= 6 have two FP64 kernels: Rys quadrature (4 or 5 nodes
+    of the Boys weight) and the Obara-Saika vertical recurrence.  HF_RYS takes Rys for all five,
+    HF_OBARA_SAIKA takes Obara-Saika for all, the default takes Rys for (dp|dp), (dd|ds), (dd|dp), (dd|dd).
+    All three against the oracle's unscreened J and K (McMurchie-Davidson) at 4 waters within 1e-10 and
+    against each other to rounding; then with Schwarz and primitive screening at 8 waters against each
+    other."""
     from paper_1708_00033_gb300 import hf
     geom = I.water_cluster(4, I.CONFIG_SINGLE_BUILD)
     basis = I.synthetic_basis(geom)
@@ -346,11 +348,13 @@ def test_rys_quadrature_classes(ctx, oracle_mod):
     P = _density(oracle_mod, mol, 20, I.CONFIG_SINGLE_BUILD, 0)
     J, K = mol.jk_unique(P)
     s = hf.System(ctx, geom, basis)
-    os_ = s.fock_build(P, want_J=True, want_K=True)
+    os_ = s.fock_build(P, want_J=True, want_K=True, rys=False)
     ry = s.fock_build(P, want_J=True, want_K=True, rys=True, stats=True)
-    assert np.abs(ry["J"] - J).max() <= 1e-10 and np.abs(ry["K"] - K).max() <= 1e-10
+    de = s.fock_build(P, want_J=True, want_K=True)
     scale = np.abs(os_["F"]).max()
-    assert np.abs(ry["F"] - os_["F"]).max() <= 1e-13 * scale
+    for r in (os_, ry, de):
+        assert np.abs(r["J"] - J).max() <= 1e-10 and np.abs(r["K"] - K).max() <= 1e-10
+        assert np.abs(r["F"] - os_["F"]).max() <= 1e-13 * scale
     names = [hf.CLASS_NAMES[c] for c in range(hf.NUM_CLASSES) if ry["stats"]["class_quartets_fp64"][c] > 0]
     assert "(dd|dd)" in names and "(dp|dp)" in names
     g8 = I.water_cluster(8, 2, 3)
@@ -358,6 +362,6 @@ def test_rys_quadrature_classes(ctx, oracle_mod):
     s8 = hf.System(ctx, g8, b8, schwarz_tau=1e-10, prim_tau=I.BENCH_PRIM_TAU)
     m8 = oracle_mod.Molecule(g8, b8)
     P8 = _density(oracle_mod, m8, 40, 2, 3)
-    a = s8.fock_build(P8, want_J=True, want_K=True)
-    b = s8.fock_build(P8, want_J=True, want_K=True, rys=True)
-    assert np.abs(a["J"] - b["J"]).max() <= 1e-12 and np.abs(a["K"] - b["K"]).max() <= 1e-12
+    a = s8.fock_build(P8, want_J=True, want_K=True, rys=False)
+    for b in (s8.fock_build(P8, want_J=True, want_K=True, rys=True), s8.fock_build(P8, want_J=True, want_K=True)):
+        assert np.abs(a["J"] - b["J"]).max() <= 1e-12 and np.abs(a["K"] - b["K"]).max() <= 1e-12
