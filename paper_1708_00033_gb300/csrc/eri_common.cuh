@@ -238,11 +238,73 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
     return fmaxf(m, fmaxf(d[hb.B * n + hk.A], d[hb.A * n + hk.B]));
 }
 
+// Number of surviving primitive quartets of a shell quartet (the length of its primitive staircase):
+// bra primitive ib pairs with the first c(ib) ket primitives whose bound product reaches ptau, c
+// non-increasing as the records are sorted by bound.
+template <typename real, typename KV>
+__device__ __forceinline__ int staircase_total(const PrimPair<real>* __restrict__ bpp, int nbp, const KV& kv,
+                                               int nkp, float ptau)
+{
+    int total = 0;
+    for (int ib = 0, c = nkp; ib < nbp; ib++) {
+        const float Bb = bpp[ib].B;
+        while (c > 0 && Bb * kv.B(c - 1) < ptau) c--;
+        if (c == 0) break;
+        total += c;
+    }
+    return total;
+}
+
+// Quartet scheduling inside a warp.  Each warp takes a window of W = R * 32 / GK consecutive quartets of
+// the launch (R rounds of 32 / GK quartets), computes every quartet's staircase length, sorts the window by
+// it (bitonic sort in the warp's shared memory; key = length << 16 | position) and runs the R rounds in
+// sorted order, so that the lanes of a round have primitive loops of similar length and idle less while
+// the longest one runs.  R is the largest power of two <= kSortRounds that still gives every warp two
+// windows; with R = 1 the window is one round in launch order.
+constexpr int kSortRounds = 8;
+
+template <typename real, bool SOA>
+__device__ __forceinline__ unsigned quartet_sort_key(const EriArgs& a, const PrimPair<real>* prims, long long q,
+                                                     int pos, float ptau)
+{
+    if (q >= a.n_quartets) return (unsigned)pos;
+    const long long c = q >> kChunkShift;
+    const int b = a.chunk ? find_bra_in(a.offsets, a.chunk[c], a.chunk[c + 1], q) : find_bra(a.offsets, a.n_bra, q);
+    const int k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);
+    const PairHdr& hb = a.bhdr[b];
+    const PairHdr& hk = a.khdr[k];
+    int t;
+    if constexpr (SOA)
+        t = staircase_total(prims + hb.prim0, hb.nprim, KetSoa<real>{(const real*)a.kt + k, a.ktB + k, a.kstride},
+                            hk.nprim, ptau);
+    else
+        t = staircase_total(prims + hb.prim0, hb.nprim, KetAos<real>{prims + hk.prim0}, hk.nprim, ptau);
+    return ((unsigned)min(t, 0xFFFF) << 16) | (unsigned)pos;
+}
+
+// ascending bitonic sort of n (a power of two) keys by the 32 lanes of one warp
+__device__ __forceinline__ void warp_bitonic_sort(unsigned* k, int n, int lane32)
+{
+    for (int size = 2; size <= n; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane32; i < (n >> 1); i += 32) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const unsigned x = k[lo], y = k[hi];
+                if ((x > y) == ((lo & size) == 0)) {
+                    k[lo] = y;
+                    k[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+}
+
 }  // namespace hf
 
 // Kernels and host launchers of one class.  The digestion weight of a unique
 // shell quartet is f = 1/((1+d_AB)(1+d_CD)(1+d_AB,CD)).
-#define ERI_KERNEL_BODY(QFN)                                                                                 \
+#define ERI_KERNEL_BODY(QFN, SORT)                                                                           \
     {                                                                                                        \
         if (a.bad && *a.bad) return; /* rejected density: grid-uniform exit, outputs untouched */            \
         const PrimPair<real>* prims = (const PrimPair<real>*)(sizeof(real) == 8 ? a.prims64 : a.prims32);   \
@@ -254,45 +316,63 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
         double* const Kt = a.Kt + cofs;                                                                      \
         unsigned nprimq = 0;                                                                                 \
         constexpr int gpw = 32 / GK;                                                                         \
+        constexpr int kWmax = (SORT) ? kSortRounds * gpw : 1;                                               \
+        __shared__ unsigned skeys[(kEriThreads / 32) * kWmax];                                               \
+        unsigned* const wkeys = skeys + (threadIdx.x >> 5) * kWmax;                                          \
+        const int lane32 = threadIdx.x & 31;                                                                 \
         const int lane = threadIdx.x & (GK - 1);                                                             \
-        const int grp = (threadIdx.x & 31) / GK;                                                             \
+        const int grp = lane32 / GK;                                                                         \
         const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                      \
         const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;                                   \
-        for (long long wb = a.q_begin + warp * gpw; wb < a.n_quartets; wb += nwarps * gpw) { /* warp-uniform */ \
-            const long long q = wb + grp;                                                                    \
-            const bool valid = q < a.n_quartets;                                                             \
-            PairHdr hb, hk;                                                                                  \
-            real f = real(1);                                                                                \
-            int k = 0;                                                                                       \
-            if (valid) {                                                                                     \
-                const long long c = q >> kChunkShift;                                                        \
-                const int b = a.chunk ? find_bra_in(a.offsets, a.chunk[c], a.chunk[c + 1], q)                 \
-                                      : find_bra(a.offsets, a.n_bra, q);                                     \
-                k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                                  \
-                hb = a.bhdr[b];                                                                              \
-                hk = a.khdr[k];                                                                              \
-                if (hb.A == hb.B) f *= real(0.5);                                                            \
-                if (hk.A == hk.B) f *= real(0.5);                                                            \
-                if (a.same && b == k) f *= real(0.5);                                                        \
-            } else {                                                                                         \
-                hb = hk = a.bhdr[0];                                                                         \
+        int R = 1; /* rounds per window (grid-uniform; 1 in kernels compiled without the sort) */            \
+        if ((SORT) && a.sort_work)                                                                           \
+            while (R < kSortRounds && (long long)(2 * R) * gpw * nwarps * 2 <= a.n_quartets - a.q_begin) R *= 2; \
+        const int W = R * gpw;                                                                               \
+        for (long long wb = a.q_begin + warp * W; wb < a.n_quartets; wb += nwarps * W) { /* warp-uniform */  \
+            if ((SORT) && R > 1) {                                                                           \
+                for (int pos = lane32; pos < W; pos += 32)                                                   \
+                    wkeys[pos] = quartet_sort_key<real, SOA>(a, prims, wb + pos, pos, ptau);                 \
+                __syncwarp();                                                                                \
+                warp_bitonic_sort(wkeys, W, lane32);                                                         \
             }                                                                                                \
-            bool live = valid;                                                                               \
-            float pt = ptau;                                                                                 \
-            if (a.dsh) { /* density-weighted screening (warp-uniform branch) */                              \
-                const float dm = valid ? density_block_max(a, hb, hk) : 0.0f;                                \
-                live = valid && 4.0f * (float)(hb.Q * hk.Q) * dm >= a.dtau;                                  \
-                pt = ptau / fmaxf(dm, 1e-30f);                                                               \
+            for (int r = 0; r < R; r++) {                                                                    \
+                const int s = r * gpw + grp;                                                                 \
+                const long long q = wb + ((SORT) && R > 1 ? (long long)(wkeys[s] & 0xFFFFu) : (long long)s); \
+                const bool valid = q < a.n_quartets;                                                         \
+                PairHdr hb, hk;                                                                              \
+                real f = real(1);                                                                            \
+                int k = 0;                                                                                   \
+                if (valid) {                                                                                 \
+                    const long long c = q >> kChunkShift;                                                    \
+                    const int b = a.chunk ? find_bra_in(a.offsets, a.chunk[c], a.chunk[c + 1], q)             \
+                                          : find_bra(a.offsets, a.n_bra, q);                                 \
+                    k = (int)(q - a.offsets[b]) + (a.kstart ? a.kstart[b] : 0);                              \
+                    hb = a.bhdr[b];                                                                          \
+                    hk = a.khdr[k];                                                                          \
+                    if (hb.A == hb.B) f *= real(0.5);                                                        \
+                    if (hk.A == hk.B) f *= real(0.5);                                                        \
+                    if (a.same && b == k) f *= real(0.5);                                                    \
+                } else {                                                                                     \
+                    hb = hk = a.bhdr[0];                                                                     \
+                }                                                                                            \
+                bool live = valid;                                                                           \
+                float pt = ptau;                                                                             \
+                if (a.dsh) { /* density-weighted screening (warp-uniform branch) */                          \
+                    const float dm = valid ? density_block_max(a, hb, hk) : 0.0f;                            \
+                    live = valid && 4.0f * (float)(hb.Q * hk.Q) * dm >= a.dtau;                              \
+                    pt = ptau / fmaxf(dm, 1e-30f);                                                           \
+                }                                                                                            \
+                if constexpr (SOA) {                                                                         \
+                    const KetSoa<real> kv{(const real*)a.kt + k, a.ktB + k, a.kstride};                      \
+                    nprimq += QFN<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,     \
+                                            live);                                                           \
+                } else {                                                                                     \
+                    const KetAos<real> kv{prims + hk.prim0};                                                 \
+                    nprimq += QFN<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,     \
+                                            live);                                                           \
+                }                                                                                            \
             }                                                                                                \
-            if constexpr (SOA) {                                                                             \
-                const KetSoa<real> kv{(const real*)a.kt + k, a.ktB + k, a.kstride};                          \
-                nprimq += QFN<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
-                                                   live);                                                    \
-            } else {                                                                                         \
-                const KetAos<real> kv{prims + hk.prim0};                                         \
-                nprimq += QFN<real, GK>(hb, hk, kv, prims, bt, P, a.N, f, Jt, Kt, nullptr, pt, lane,  \
-                                                   live);                                                    \
-            }                                                                                                \
+            __syncwarp();                                                                                    \
         }                                                                                                    \
         if (a.prim_count) {                                                                                  \
             const unsigned long long w = __reduce_add_sync(0xffffffffu, nprimq);                            \
@@ -303,7 +383,7 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
 #define ERI_CLASS_KERNELS(NAME, X, Y, GL)                                                                    \
     template <typename real, int GK, bool SOA>                                                               \
     __global__ void __launch_bounds__(kEriThreads) k_eri_##NAME(const EriArgs a)                            \
-    ERI_KERNEL_BODY(quartet_##NAME)                                                                          \
+    ERI_KERNEL_BODY(quartet_##NAME, true)                                                                    \
     void launch_eri_##NAME(const EriArgs& a, int use_f32, int grid, int block, cudaStream_t s, int lanes)   \
     {                                                                                                        \
         if (use_f32)                                                                                         \
@@ -330,7 +410,7 @@ __device__ __forceinline__ float density_block_max(const A& a, const PairHdr& hb
 #define ERI_RYS_KERNELS(NAME, GL)                                                                            \
     template <typename real, int GK, bool SOA>                                                               \
     __global__ void __launch_bounds__(kEriThreads) k_eri_rys_##NAME(const EriArgs a)                        \
-    ERI_KERNEL_BODY(quartet_rys_##NAME)                                                                      \
+    ERI_KERNEL_BODY(quartet_rys_##NAME, false)                                                               \
     void launch_eri_rys_##NAME(const EriArgs& a, int, int grid, int block, cudaStream_t s, int lanes)       \
     {                                                                                                        \
         if (lanes > 1)                                                                                       \

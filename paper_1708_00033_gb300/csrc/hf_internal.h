@@ -63,6 +63,7 @@ struct EriArgs {
     long long kstride;                // kets per field row of the ket table
     const PairHdr* bhdr;              // headers of the bra list in list order (bhdr[b] = pairs[bra[b]])
     const PairHdr* khdr;              // headers of the ket list in list order (khdr[k] = pairs[ket[k]])
+    int sort_work;                    // 1: each warp runs its window of quartets sorted by staircase length
 };
 
 struct SchwarzArgs {
