@@ -757,6 +757,7 @@ int hf::launch_eri_classes(hf_system* S, EriArgs a, int shard, int n_shards, int
                 const int grid = (int)std::min<long long>(blocks, (long long)ctx->num_sms * 16);
                 // FP64 launches run each warp's window of quartets sorted by staircase length (64 waters:
                 // 2% faster); the FP32 kernels, bound by latency rather than a pipe, ran 10% slower with it
+                // and are compiled without it
                 a.sort_work = use_f32 ? 0 : 1;
                 if (uses_rys(ci, flags, use_f32, a))
                     kEriClasses[ci].launch_rys(a, 0, grid, kEriThreads, st, lanes);

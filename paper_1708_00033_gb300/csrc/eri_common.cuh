@@ -62,16 +62,26 @@ struct KetSoa {
     __device__ __forceinline__ float B(int i) const { return __ldg(fB + (long long)i * stride); }
 };
 
-// Boys tables in Taylor-coefficient form, so that evaluation is a pure Horner chain (T < 60):
-//   FP64 rows T_k = k / 512, k = 0..kBoysRows64-1:
-//             c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..4) at m*5 + j,
-//             e^{-T_k} / j! (j = 0..4) at 45 + j;
-//   FP32 rows T_k = k / 32, k = 0..kBoysRows32-1:
+// Boys tables in Taylor-coefficient form, so that evaluation is a pure Horner chain:
+//   FP64 rows, two regions of one table:
+//     A: T_k = k / 512 for k = 0..kBoysRowsA-1 (T < 64): c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..4)
+//        at m*5 + j, and e^{-T_k} / j! (j = 0..4) at 45 + j;
+//     B: T_k = 2^e (1 + i / 4096), e = 6..31, i = 0..4095 (64 <= T < 2^31): the same coefficients of the
+//        asymptotic form F_m(T) = (2m-1)!! / 2^(m+1) sqrt(pi / T^(2m+1)), which is F_m to within half an
+//        ulp there (every order's switch point is below 64), with the e^{-T_k} coefficients zero;
+//   FP32 rows T_k = k / 32, k = 0..kBoysRows32-1 (T < 60):
 //             c[m][j] = F_{m+j}(T_k) / j!  (m = 0..8, j = 0..3) at m*4 + j,
 //             e^{-T_k} / j! (j = 0..4) at 36 + j.
-// The FP64 grid is fine so that each FP64 Horner chain is short: FP64 instructions are the scarce
-// resource of the ERI kernels, table loads are not.
-constexpr int kBoysRows64 = 60 * 512 + 1;
+// One FP64 table over both regions gives every lane of a warp the same instruction stream whatever its
+// T (no Taylor/asymptotic branch to diverge on); the grids are fine so that each Horner chain is short.
+// FP64 instructions are the scarce resource of the ERI kernels, table loads are not.
+constexpr int kBoysRowsA = 64 * 512 + 1;
+constexpr int kBoysBinade0 = 6;    // region B starts at 2^6 = 64
+constexpr int kBoysBinades = 26;   // binades 2^6 .. 2^31 (the last one only its first row)
+constexpr int kBoysSubBits = 12;   // 4096 rows per binade
+constexpr int kBoysRows64 = kBoysRowsA + (kBoysBinades << kBoysSubBits);
+constexpr long long kBoysBitsB = 0x4050000000000000LL;    // bit pattern of 64.0
+constexpr long long kBoysBitsTop = 0x41E0000000000000LL;  // bit pattern of 2^31
 constexpr int kBoysRows32 = 60 * 32 + 1;
 constexpr int kBoysStride64 = 50;
 constexpr int kBoysStride32 = 44;
@@ -85,7 +95,8 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // Switch points of the asymptotic form F_m(T) ~ (2m-1)!! / 2^(m+1) sqrt(pi / T^(2m+1)), by the highest
 // order L evaluated: from these T on, its relative error (the dropped terms carry e^{-T}) is below half
 // an ulp for every m <= L, in FP64 (2^-54) and FP32 (2^-25), computed from the incomplete gamma function
-// at 40 digits.  Below them the Taylor tables are used.
+// at 40 digits.  FP32: below them the Taylor table, above them the asymptotic form.  FP64: the asymptotic
+// rows of the table (region B) start at 64, above every order's switch point.
 __host__ __device__ constexpr double boys_switch64(int L)
 {
     return L == 0 ? 36.0 : L == 1 ? 40.0 : L == 2 ? 43.0 : L == 3 ? 46.0 : L == 4 ? 49.0 : L == 5 ? 52.0
@@ -97,22 +108,34 @@ __host__ __device__ constexpr float boys_switch32(int L)
          : L == 6 ? 31.0f : L == 7 ? 33.0f : 35.0f;
 }
 
-// F_m(T), m = 0..L.  Below boys_switch64(L) (<= 59, inside the tables' T < 60): Taylor expansion about the
-// nearest grid point T_k (|T - T_k| <= 1/1024; five terms, truncation below (1/1024)^5 / 5! < 1e-17
-// relative, as |F_{m+5}| <= |F_m|), using dF_m/dT = -F_{m+1}; for L >= 2 only F_L is expanded and the rest
-// follow from the downward recursion F_m = (2T F_{m+1} + e^{-T}) / (2m+1), with e^{-T} = e^{-T_k} e^{T_k - T}
-// expanded the same way.  Above: F_0 = sqrt(pi/T)/2 and the upward recursion F_{m+1} = (2m+1) F_m / (2T)
-// (the e^{-T} terms dropped).  The grid index is the integer that T*512 + 1.5*2^52 rounds to, read from the
-// low word of the sum.
+// F_m(T), m = 0..L, FP64.  Taylor expansion about the nearest row T_k of the table (region A: |T - T_k| <=
+// 1/1024, five terms, truncation below (1/1024)^5 / 5! < 1e-17 relative, as |F_{m+5}| <= |F_m|; region B:
+// |T - T_k| <= T / 8192, where the asymptotic form's fifth-order term is below 2e-17 relative for m <= 8),
+// using dF_m/dT = -F_{m+1}, which the asymptotic form obeys as well.  For L >= 2 only F_L is expanded and
+// the rest follow from the downward recursion F_m = (2T F_{m+1} + e^{-T}) / (2m+1), with e^{-T} =
+// e^{-T_k} e^{T_k - T} expanded the same way (zero in region B).  Region A's row is the integer that
+// T*512 + 1.5*2^52 rounds to, read from the low word of the sum; region B's row and T_k come from T's bit
+// pattern rounded to 12 mantissa bits.  T >= 2^31 (far beyond any screened quartet) takes the asymptotic
+// form directly: F_0 = sqrt(pi/T)/2, F_{m+1} = (2m+1) F_m / (2T).
+static_assert(boys_switch64(8) <= 64.0, "region B of the FP64 table must lie above every switch point");
 template <int L>
 __device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double* F)
 {
-    if (T < boys_switch64(L)) {
+    const long long bits = __double_as_longlong(T);
+    if (bits < kBoysBitsTop) {
         const double big = 6755399441055744.0;  // 1.5 * 2^52
         const double t = fma(T, 512.0, big);
-        const int k = __double2loint(t);
-        const double d = fma(t - big, 1.0 / 512.0, -T);  // T_k - T
-        const double* __restrict__ r = tab + k * kBoysStride64;
+        int k = __double2loint(t);
+        double d = fma(t - big, 1.0 / 512.0, -T);  // T_k - T (region A)
+        const long long rb = bits + (1LL << (51 - kBoysSubBits));
+        const double Tk = __longlong_as_double(rb & ~((1LL << (52 - kBoysSubBits)) - 1));
+        const double dB = Tk - T;
+        if (bits >= kBoysBitsB) {
+            k = kBoysRowsA + (((int)(rb >> 52) - 1023 - kBoysBinade0) << kBoysSubBits)
+              + (int)((rb >> (52 - kBoysSubBits)) & ((1 << kBoysSubBits) - 1));
+            d = dB;
+        }
+        const double* __restrict__ r = tab + (size_t)k * kBoysStride64;
         if constexpr (L <= 1) {
 #pragma unroll
             for (int m = 0; m <= L; m++) {
@@ -316,7 +339,8 @@ __device__ __forceinline__ void warp_bitonic_sort(unsigned* k, int n, int lane32
         double* const Kt = a.Kt + cofs;                                                                      \
         unsigned nprimq = 0;                                                                                 \
         constexpr int gpw = 32 / GK;                                                                         \
-        constexpr int kWmax = (SORT) ? kSortRounds * gpw : 1;                                               \
+        constexpr bool kSort = (SORT) && sizeof(real) == 8; /* FP32 launches run in launch order */         \
+        constexpr int kWmax = kSort ? kSortRounds * gpw : 1;                                                 \
         __shared__ unsigned skeys[(kEriThreads / 32) * kWmax];                                               \
         unsigned* const wkeys = skeys + (threadIdx.x >> 5) * kWmax;                                          \
         const int lane32 = threadIdx.x & 31;                                                                 \
@@ -325,11 +349,11 @@ __device__ __forceinline__ void warp_bitonic_sort(unsigned* k, int n, int lane32
         const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                      \
         const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;                                   \
         int R = 1; /* rounds per window (grid-uniform; 1 in kernels compiled without the sort) */            \
-        if ((SORT) && a.sort_work)                                                                           \
+        if (kSort && a.sort_work)                                                                            \
             while (R < kSortRounds && (long long)(2 * R) * gpw * nwarps * 2 <= a.n_quartets - a.q_begin) R *= 2; \
         const int W = R * gpw;                                                                               \
         for (long long wb = a.q_begin + warp * W; wb < a.n_quartets; wb += nwarps * W) { /* warp-uniform */  \
-            if ((SORT) && R > 1) {                                                                           \
+            if (kSort && R > 1) {                                                                            \
                 for (int pos = lane32; pos < W; pos += 32)                                                   \
                     wkeys[pos] = quartet_sort_key<real, SOA>(a, prims, wb + pos, pos, ptau);                 \
                 __syncwarp();                                                                                \
@@ -337,7 +361,7 @@ __device__ __forceinline__ void warp_bitonic_sort(unsigned* k, int n, int lane32
             }                                                                                                \
             for (int r = 0; r < R; r++) {                                                                    \
                 const int s = r * gpw + grp;                                                                 \
-                const long long q = wb + ((SORT) && R > 1 ? (long long)(wkeys[s] & 0xFFFFu) : (long long)s); \
+                const long long q = wb + (kSort && R > 1 ? (long long)(wkeys[s] & 0xFFFFu) : (long long)s);  \
                 const bool valid = q < a.n_quartets;                                                         \
                 PairHdr hb, hk;                                                                              \
                 real f = real(1);                                                                            \

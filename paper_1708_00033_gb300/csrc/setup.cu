@@ -11,7 +11,7 @@
 namespace hf {
 
 // ------------------------------------------------------------ Boys table --
-// F_m(T_k), m = 0..14, at the grid points T_k = k/512 (FP64 table) and k/32 (FP32 table): the series
+// F_m(T_k), m = 0..14, at the grid points T_k = k/512 (FP64 table, T < 64) and k/32 (FP32 table): the series
 //   F_M(T) = exp(-T) sum_i (2T)^i / ((2M+1)(2M+3)...(2M+2i+1))
 // for the top order (compensated summation of its positive terms), then the
 // downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1); stored as the
@@ -37,8 +37,18 @@ __global__ void k_boys_table(double* t64, float* t32)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double F[15], e;
-    if (k < kBoysRows64) {
+    if (k < kBoysRowsA) {
         boys_row(k / 512.0, F, e);
+    } else if (k < kBoysRows64) {
+        // region B: the asymptotic form at T_k = 2^e (1 + i / 4096)
+        const int r = k - kBoysRowsA;
+        const double Tk = ldexp(1.0 + (r & ((1 << kBoysSubBits) - 1)) / (double)(1 << kBoysSubBits),
+                                kBoysBinade0 + (r >> kBoysSubBits));
+        F[0] = 0.5 * sqrt(M_PI / Tk);
+        for (int m = 0; m < 14; m++) F[m + 1] = F[m] * (2 * m + 1) / (2.0 * Tk);
+        e = 0.0;
+    }
+    if (k < kBoysRows64) {
         double* r = t64 + (size_t)k * kBoysStride64;
         double fact = 1.0;
         for (int j = 0; j <= 4; j++) {
