@@ -37,10 +37,10 @@ DFMA_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.
 # ncu capture of the default workload, with the SHA-256 of the sources that kernel is compiled from at that
 # time; the bench reports it only while those sources are unchanged (else the counters describe another
 # kernel and traffic is null).  Capture: the 64-water FP64 build at the bench's thresholds (`--mode case
-# --case fock --waters 64`), one pass, both launches of k_eri_1110<double>: 397.73 + 87.35 MB and
-# 397.39 + 87.31 MB; their mean.
-NCU_TRAFFIC = {"kernel": "k_eri_1110", "bytes_per_launch": 484.89e6,
-               "sources_sha256": "b5ca5b039cdf10120c95a1ed6330a31ed808eac85918b853eb0ea6dd11d0e845"}
+# --case fock --waters 64`), one pass, both launches of k_eri_1110<double>: 3.79 GB + 630.90 MB and
+# 3.80 GB + 632.54 MB; their mean.
+NCU_TRAFFIC = {"kernel": "k_eri_1110", "bytes_per_launch": 4.4267e9,
+               "sources_sha256": "18cdc26cad87ad9d767e774a67808fd25df6ef1a68ef13699d23cc8cda1164c0"}
 TRAFFIC_SOURCES = ("paper_1708_00033_gb300/csrc/gen_eri.py", "paper_1708_00033_gb300/csrc/eri_common.cuh",
                    "paper_1708_00033_gb300/csrc/hf_internal.h")
 
