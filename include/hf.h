@@ -205,9 +205,9 @@ int hf_one_electron(hf_system* sys, double* S, double* H, int flags);
  *   E_elec host scalar output 1/2 sum P (H + F) (may be NULL).
  *   stats  host output (may be NULL); HF_TIMING adds device times.
  * flags: HF_PTR_DEVICE (P, F, J, K are device pointers), HF_TIMING,
- * HF_FP64_ONLY, HF_RYS.  The density check runs on the device: the host waits once,
- * after the whole build, and a rejected density leaves every output
- * untouched.
+ * HF_FP64_ONLY, HF_RYS, HF_OBARA_SAIKA.  The density check runs on the device:
+ * the host waits once, after the whole build, and a rejected density leaves
+ * every output untouched.
  * Errors: HF_E_INVALID (NULL sys/P, P not finite or not symmetric),
  * HF_E_NOMEM, HF_E_CUDA. */
 int hf_fock_build(hf_system* sys, const double* P, double* F, double* J, double* K, double* E_elec, hf_stats* stats,
@@ -253,7 +253,7 @@ int hf_system_set_fock_copies(hf_system* sys, int32_t copies);
  * 1/2 sum_s K_s: the counterpart of the paper's per-rank partial Fock matrix
  * and ddi_gsumf (Algorithms 1-3), with the sum left to the caller (for
  * example one allreduce of J and K).  J, K: [N*N] outputs (required).
- * flags: HF_PTR_DEVICE, HF_FP64_ONLY, HF_RYS, HF_DENSITY_SCREEN (density-weighted
+ * flags: HF_PTR_DEVICE, HF_FP64_ONLY, HF_RYS, HF_OBARA_SAIKA, HF_DENSITY_SCREEN (density-weighted
  * Schwarz screening: the J and K of a density difference, as in incremental
  * SCF builds).  Errors: HF_E_INVALID (bad shard, NULL pointer, P not finite
  * or not symmetric), HF_E_CUDA. */
