@@ -94,3 +94,23 @@ def test_binding_holds_no_method_arithmetic():
                 if isinstance(node.left, kinds) and isinstance(node.right, kinds):
                     names = {n.id for n in ast.walk(node) if isinstance(n, ast.Name)}
                     assert not names & {"H", "J", "K", "F", "P", "S", "C"}, (name, node.lineno)
+
+
+def test_binding_constants_match_header():
+    """Every HF_* integer constant of the binding equals the header's #define of that name, and every flag
+    and status code the header defines exists in the binding."""
+    import re
+    from paper_1708_00033_gb300 import hf
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    txt = open(os.path.join(root, "include", "hf.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (HF_\w+)\s+(-?\d+)\b", txt, re.M)}
+    assert defs["HF_OBARA_SAIKA"] == 64 and defs["HF_RYS"] == 32
+    for name, value in vars(hf).items():
+        if name.startswith("HF_") and isinstance(value, int) and name in defs:
+            assert value == defs[name], name
+    for name in defs:
+        if name.startswith(("HF_E_", "HF_PTR_")) or name in ("HF_OK", "HF_TIMING", "HF_FP64_ONLY", "HF_DENSITY_SCREEN",
+                                                              "HF_RYS", "HF_OBARA_SAIKA", "HF_SP_SHELL",
+                                                              "HF_BATCH_SEQUENTIAL"):
+            assert getattr(hf, name) == defs[name], name
+    assert hf.NUM_CLASSES == defs["HF_NUM_CLASSES"]
